@@ -1,0 +1,414 @@
+#!/usr/bin/env python3
+"""Throughput of the all-sky F-statistic search on GB300: F-statistic evaluations
+per second (sky x spindown x searched bin), FP32 batched form, with the plain
+FP64 form, the roofline fraction of the dominant kernel, an end-to-end number
+through the C ABI with host buffers, and the FP64 CPU oracle as a baseline.
+
+One step = one fstat_search over the whole grid: per band the noise variance and
+the FFT upsample, per sky position the geometry / resampling / phase
+demodulation, per cell the spindown demodulation, two zero-padded FFTs, F per
+bin, threshold and candidate compaction.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun each rank searches its own block of sky positions of an N-times
+larger grid (weak scaling, no data-path collective); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "F-stat evals/s (sky×spindown×bin) on 1 GB300: FP32-batched vs FP64 plain, % roofline"
+UNIT = "F-evals/s"
+SMS, FP32_LANES = 152, 128          # GB300: SMs, FP32 lanes per SM
+L2_BYTES = 129 << 20
+
+
+def fp32_peak_tflops(mhz: float) -> float:
+    return SMS * FP32_LANES * 2 * mhz * 1e6 / 1e12
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh)
+    except OSError:
+        return {}
+
+
+# ----------------------------------------------------------------------------- clocks
+class Clocks:
+    """nvidia-smi sampling during the timed region (SM clock, throttle reasons)."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as fh:
+            for line in fh:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for name, v in zip(names, r[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(rows)}
+
+
+# ----------------------------------------------------------------------------- workload
+def make_workload(world: int, rank: int):
+    """The precision workload: one band of N = 86164 samples (two sidereal days at
+    2 s), 4096 sky positions x 64 spindowns in [-1e-8, 0] Hz/s, N_fft = 2^18,
+    16 injected signals, 2F > 30.  Under N ranks, rank r takes sky block r of a
+    4096*N-point Fibonacci grid."""
+    from paper_1410_3677_gb300 import synth as S
+    w = S.workload(3)
+    if world > 1:
+        a, d = S.fibonacci_sky(4096 * world)
+        w.alpha, w.delta = a[rank::world].copy(), d[rank::world].copy()
+    return w
+
+
+def sample_cells(w, n_cells):
+    """A bounded, deterministic sample of cells: whole sky positions (all
+    spindowns) spread over the grid."""
+    n_sky = max(1, math.ceil(n_cells / w.n_spin))
+    skies = np.linspace(0, w.n_sky - 1, n_sky).astype(np.int64)
+    cs = np.repeat(skies, w.n_spin)[:n_cells]
+    cp = np.tile(np.arange(w.n_spin), n_sky)[:n_cells]
+    return cs, cp
+
+
+def oracle_rate(w, target_s=15.0):
+    """FP64 CPU oracle F-evals/s on a bounded sample of the workload's cells."""
+    import oracle as O
+    prm = O.params(w.lat, w.gamma, w.upsample, 0.0, False, 0)
+    threads = os.cpu_count() or 1
+    b = w.bands[0]
+    nb = b.n_fft // 2 - 1
+    cs, cp = sample_cells(w, threads)
+    t0 = time.perf_counter()
+    O.cells_F(b, prm, w.alpha, w.delta, w.fdot, cs, cp, nthreads=threads)
+    per_cell = (time.perf_counter() - t0) / max(cs.size, 1)
+    n = int(max(threads, min(4096, target_s / max(per_cell, 1e-6))))
+    n = max(threads, (n // threads) * threads)
+    cs, cp = sample_cells(w, n)
+    t0 = time.perf_counter()
+    O.cells_F(b, prm, w.alpha, w.delta, w.fdot, cs, cp, nthreads=threads)
+    el = time.perf_counter() - t0
+    return {"value": cs.size * nb / el, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"{cs.size} cells ({cs.size // w.n_spin} sky positions x {w.n_spin} "
+                      f"spindowns) of the 4096x64 grid, N_fft=2^18, all {nb} bins, "
+                      f"{el:.1f} s"}
+
+
+# ----------------------------------------------------------------------------- reference arm
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    from paper_1410_3677_gb300 import synth as S
+    w = make_workload(1, 0)
+    import oracle as O
+    prm = O.params(w.lat, w.gamma, w.upsample, 0.0, False, 0)
+    threads = os.cpu_count() or 1
+    nb = w.bands[0].n_fft // 2 - 1
+    # size each step to a few seconds of CPU work
+    cs, cp = sample_cells(w, threads)
+    t0 = time.perf_counter()
+    O.cells_F(w.bands[0], prm, w.alpha, w.delta, w.fdot, cs, cp, nthreads=threads)
+    per_cell = (time.perf_counter() - t0) / cs.size
+    budget = 150.0 / max(args.steps + args.warmup, 1)
+    n = max(threads, int(budget / per_cell) // threads * threads)
+    cs, cp = sample_cells(w, n)
+    for _ in range(args.warmup):
+        O.cells_F(w.bands[0], prm, w.alpha, w.delta, w.fdot, cs[:threads], cp[:threads],
+                  nthreads=threads)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        O.cells_F(w.bands[0], prm, w.alpha, w.delta, w.fdot, cs, cp, nthreads=threads)
+        times.append(time.perf_counter() - t0)
+    tot = sum(times)
+    value = cs.size * nb * args.steps / tot
+    sample = (f"{cs.size} cells per step ({cs.size // w.n_spin} sky positions x {w.n_spin} "
+              f"spindowns) of the 4096x64 grid, all {nb} bins")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": "precision: N=86164, N_fft=2^18, 4096 sky x 64 spindown",
+                       "form": "fp64 cpu oracle", "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ----------------------------------------------------------------------------- our arm
+def traffic_record(kernel_name):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on the
+    current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as fh:
+            rec = json.load(fh)
+    except OSError:
+        return None
+    src = source_hash()
+    k = rec.get(kernel_name)
+    if not k or k.get("source_hash") != src:
+        return None
+    return k.get("dram_bytes_per_launch")
+
+
+def source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1410_3677_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def run_ours(args, rank, world, dist):
+    import torch
+    from paper_1410_3677_gb300 import fstat
+    dev = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(dev)
+    w = make_workload(world, rank)
+    stream = torch.cuda.Stream()
+    nb_total = w.f_evals()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    # ---------------------------------------------------------------- device-resident value
+    plan = fstat.Plan(w.bands, w.alpha, w.delta, w.fdot, w.thr_2F, lat=w.lat, gamma=w.gamma,
+                      upsample=w.upsample, form=fstat.FP32_BATCHED, cand_capacity=1 << 24,
+                      stream=stream.cuda_stream)
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
+    for _ in range(args.warmup):
+        plan.search()
+    plan.set_timing(args.sample_every)
+    launches0 = plan.info()["kernel_launches"]
+    clocks = Clocks(dev)
+    torch.cuda.synchronize()
+    barrier()
+    clocks.start()
+    t_wall0 = time.perf_counter()
+    step_ms = []
+    for _ in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.add_(1.0)                       # evict L2 between steps
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        plan.search()
+        e1.record(stream)
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter() - t_wall0
+    barrier()
+    clk = clocks.stop()
+    launches = plan.info()["kernel_launches"] - launches0
+    kstats = plan.kernel_stats()
+    cands, n_total = plan.candidates()
+    plan.close()
+    tot_ms = sum(step_ms)
+    if dist is not None:
+        t = torch.tensor([tot_ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        tot_ms = float(t.item())
+    value = nb_total * world * args.steps / (tot_ms / 1e3)
+
+    # ---------------------------------------------------------------- roofline of the dominant kernel
+    peaks = measured_peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    dom = max(((k, v) for k, v in kstats.items() if v["timed_launches"] > 0),
+              key=lambda kv: kv[1]["timed_ms"] / kv[1]["timed_launches"] * kv[1]["launches"])
+    dname, dv = dom
+    avg_ms = dv["timed_ms"] / dv["timed_launches"]
+    achieved = dv["flops_per_launch"] / (avg_ms / 1e3) / 1e12
+    peak = fp32_peak_tflops(sm_max)
+    shares = {k: round(v["timed_ms"] / v["timed_launches"] * v["launches"] / tot_ms * args.steps
+                       / args.steps, 4) if v["timed_launches"] else None for k, v in kstats.items()}
+    roofline = {"bound": "alu", "kernel": dname, "achieved": round(achieved, 3),
+                "peak": round(peak, 2), "unit": "TFLOP/s", "frac": round(achieved / peak, 4),
+                "traffic": traffic_record(dname),
+                "peak_basis": f"{SMS} SMs x {FP32_LANES} FP32 lanes x 2 flop/FMA x {sm_max:.0f} MHz (max SM clock)",
+                "flops_per_launch": dv["flops_per_launch"], "avg_launch_ms": round(avg_ms, 5),
+                "timed_launches": dv["timed_launches"], "kernel_time_share": shares}
+    if clk and clk.get("sm_mhz"):
+        roofline["frac_at_measured_clock"] = round(achieved / fp32_peak_tflops(clk["sm_mhz"]), 4)
+
+    # ---------------------------------------------------------------- plain FP64 form on a subgrid
+    fp64 = None
+    if not args.skip_fp64:
+        sub = 64
+        p64 = fstat.Plan(w.bands, w.alpha[:sub], w.delta[:sub], w.fdot, w.thr_2F, lat=w.lat,
+                         gamma=w.gamma, upsample=w.upsample, form=fstat.FP64_PLAIN,
+                         cand_capacity=1 << 22, stream=stream.cuda_stream)
+        p64.search(0, w.n_spin)           # warm-up on one sky position
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        p64.search()
+        e1.record(stream)
+        e1.synchronize()
+        ms64 = e0.elapsed_time(e1)
+        ev64 = p64.info()["f_evals"]
+        p64.close()
+        fp64 = {"value": ev64 / (ms64 / 1e3), "unit": UNIT, "dtype": "f64",
+                "sample": f"{sub} sky x {w.n_spin} spindown subgrid of the same workload, "
+                          f"one cell per launch pair"}
+
+    # ---------------------------------------------------------------- end to end through the C ABI
+    e2e = None
+    if not args.skip_e2e:
+        def pinned(a):
+            t = torch.empty(a.shape, dtype=getattr(torch, str(a.dtype)), pin_memory=True)
+            t.numpy()[...] = a
+            return t.numpy()
+
+        class HB:
+            pass
+        hbs = []
+        h2d = 0
+        for b in w.bands:
+            hb = HB()
+            hb.n, hb.dt, hb.f_off, hb.phi0, hb.eps, hb.n_fft = b.n, b.dt, b.f_off, b.phi0, b.eps, b.n_fft
+            hb.x = pinned(np.ascontiguousarray(b.x))
+            hb.r = pinned(np.ascontiguousarray(b.r))
+            h2d += hb.x.nbytes + hb.r.nbytes
+            hbs.append(hb)
+        al, de, fd = pinned(w.alpha), pinned(w.delta), pinned(w.fdot)
+        h2d += al.nbytes + de.nbytes + fd.nbytes
+        n_e2e = max(1, min(args.steps, 3))
+        times, d2h = [], 0
+        for it in range(n_e2e + 1):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            p = fstat.Plan(hbs, al, de, fd, w.thr_2F, lat=w.lat, gamma=w.gamma,
+                           upsample=w.upsample, form=fstat.FP32_BATCHED, cand_capacity=1 << 24,
+                           stream=stream.cuda_stream)
+            p.search()
+            c, nt = p.candidates()
+            p.close()
+            torch.cuda.synchronize()
+            if it > 0:
+                times.append(time.perf_counter() - t0)
+            d2h = int(c.size) * 16 + 8
+        e2e = {"value": nb_total * world / statistics.mean(times), "unit": UNIT,
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+               "steps": n_e2e,
+               "includes": "fstat_plan_create (device allocation + host->device copies from "
+                           "pinned memory) + fstat_search + fstat_candidates_get "
+                           "(device->host + sort) + fstat_plan_destroy"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.skip_cpu:
+        cpu = oracle_rate(w)
+
+    if rank != 0:
+        return 0
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "precision: N=86164 float64 samples (2 sidereal days at 2 s), "
+                                   "N_fft=2^18, 4096 sky x 64 spindown, 16 injections, 2F>30",
+                       "form": "fp32_batched", "n_cells": int(w.n_sky * w.n_spin),
+                       "bins_per_cell": int(w.bands[0].n_fft // 2 - 1),
+                       "l2": "a 258 MB buffer is rewritten between timed steps (L2 flushed)",
+                       "wall_s": round(t_wall, 3)},
+            "candidates": int(n_total), "gpu_launches": int(launches),
+            "roofline": roofline, "fp64_plain": fp64,
+            "speedup_vs_fp64_plain": (value / world / fp64["value"]) if fp64 else None,
+            "e2e": e2e, "cpu_baseline": cpu, "clocks": clk}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--sample-every", type=int, default=16)
+    ap.add_argument("--skip-fp64", action="store_true")
+    ap.add_argument("--skip-e2e", action="store_true")
+    ap.add_argument("--skip-cpu", action="store_true")
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch
+        import torch.distributed as td
+        backend = "nccl" if (args.impl == "ours" and torch.cuda.is_available()) else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        td.init_process_group(backend)
+        dist = td
+    try:
+        if args.impl == "reference":
+            return run_reference(args, rank, world)
+        return run_ours(args, rank, world, dist)
+    finally:
+        if dist is not None:
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    sys.exit(main())

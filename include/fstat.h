@@ -1,0 +1,194 @@
+/*
+ * fstat.h -- C ABI of libfstat.so: the all-sky F-statistic search hot path on one
+ * GB300 GPU (sm_103a), after Poghosyan et al., "Architecture, implementation and
+ * parallelization of the software to search for periodic gravitational wave
+ * signals" (CPC; arXiv:1410.3677).
+ *
+ * The problem statement follows the paper's Sect. 2: per (band, frame) the code
+ * reads a narrow-band real time series sampled at dt, the detector-to-SSB vector
+ * for every sample plus the sidereal phase phi0 at the first sample and the
+ * obliquity eps, and a grid of sky positions and spindowns.  For every
+ * (sky, spindown) cell it evaluates the F-statistic at every frequency bin of a
+ * zero-padded FFT and registers the grid points where the statistic crosses a
+ * threshold (Sect. 2 and Fig. 1: sky loop -> amplitude and phase demodulation
+ * -> resampling -> spindown loop -> spindown demodulation -> FFT -> Fourier
+ * transform interpolation -> F-statistic -> threshold).  A candidate carries the
+ * sky position, frequency, spindown and the value of F (Sect. 2).
+ *
+ * Readings of what the paper leaves unstated (it prints no formula):
+ *   F = |F_a|^2/(sigma^2 S_aa) + |F_b|^2/(sigma^2 S_bb), with F_a, F_b the
+ *   FFTs of the resampled series weighted by the amplitude modulations a(t),
+ *   b(t) of a right-angle interferometer (Jaranowski-Krolak-Schutz), S_aa, S_bb
+ *   their sums of squares over the resampled window and sigma^2 = (1/N) sum x^2
+ *   unless given; delay d = nhat . r in seconds (r in light-seconds, equatorial);
+ *   detector time of barycentric sample k by the two-step fixed point
+ *   t = k dt - d(k dt - d(k dt)) with d interpolated linearly; resampling by a
+ *   U-fold FFT upsample then Keys cubic (a = -1/2) interpolation, samples whose
+ *   detector time falls outside [0, (n-1) dt] set to zero; band-offset phase
+ *   exp(-2 pi i f_off d(t)); spindown phase exp(-i pi fdot (k dt)^2); the "twice
+ *   as long" transform as exact zero padding to n_fft >= 2n; strict 2F > thr.
+ *
+ * Conventions for every entry point:
+ *   - returns an fstat_status; nothing throws across the ABI;
+ *   - calls are synchronous with respect to the host (they return after the GPU
+ *     work they queue has finished); a plan is not thread-safe;
+ *   - the caller owns every array it passes and may free it after the call that
+ *     received it returns; the plan owns all device memory it allocates;
+ *   - after FSTAT_ERR_CUDA or FSTAT_ERR_TIMEOUT a plan is poisoned: later calls
+ *     other than fstat_plan_destroy / fstat_plan_error return FSTAT_ERR_STATE.
+ */
+#ifndef FSTAT_H
+#define FSTAT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    FSTAT_OK = 0,
+    FSTAT_ERR_ARG = 1,       /* invalid argument: nothing was done */
+    FSTAT_ERR_OOM = 2,       /* a device or host allocation failed; nothing leaked */
+    FSTAT_ERR_CUDA = 3,      /* a CUDA call failed; the plan is poisoned */
+    FSTAT_ERR_OVERFLOW = 4,  /* more candidates than capacity; totals stay exact */
+    FSTAT_ERR_TIMEOUT = 5,   /* a bounded device-side wait ran out; plan poisoned */
+    FSTAT_ERR_STATE = 6,     /* plan poisoned by an earlier error, or misuse */
+    FSTAT_ERR_INTERNAL = 7   /* an internal consistency check failed */
+} fstat_status;
+
+typedef enum {
+    FSTAT_FP64_PLAIN = 0,    /* every step in FP64, one cell at a time */
+    FSTAT_FP32_BATCHED = 1   /* FP32 resample/FFT/|F|^2, FP64 delay, phase reduction
+                                and compensated sums; many cells per launch */
+} fstat_form;
+
+/* One narrow band of one frame (Sect. 2: xdat_d_b.bin + DetSSB.bin). */
+typedef struct {
+    int64_t n;           /* samples, >= 16 */
+    double dt;           /* sampling interval, s, > 0 */
+    double f_off;        /* lower band edge, Hz (Eq. 1); enters the band-offset phase */
+    const double *x;     /* x[n] float64, or NULL when x32 is given */
+    const float *x32;    /* x[n] float32, or NULL when x is given (exactly one) */
+    const double *r;     /* r[3n]: detector->SSB vector per sample, light-seconds,
+                            equatorial, row-major (x, y, z) */
+    double phi0;         /* sidereal phase of the detector at the first sample, rad */
+    double eps;          /* obliquity of the ecliptic, rad; carried with the
+                            ephemeris as in the paper, not used (r is equatorial) */
+    int64_t n_fft;       /* transform length: 0 = smallest power of two >= 2n;
+                            else a power of two >= 2n, 256 <= n_fft <= 2^20 */
+} fstat_band;
+
+typedef struct {
+    int n_bands;                 /* >= 1 */
+    const fstat_band *bands;     /* [n_bands] */
+    int64_t n_sky;               /* >= 1 */
+    const double *alpha;         /* [n_sky] right ascension, rad */
+    const double *delta;         /* [n_sky] declination, rad */
+    int64_t n_spin;              /* >= 1 */
+    const double *fdot;          /* [n_spin] spindown, Hz/s */
+    double thr_2F;               /* register a candidate when 2F > thr_2F */
+    int64_t bin_lo, bin_hi;      /* searched bins, inclusive; 0,0 = [1, n_fft/2 - 1]
+                                    per band; else 0 <= lo <= hi < n_fft of every band */
+    double lat;                  /* detector latitude, rad */
+    double gamma;                /* arm-bisector orientation, counter-clockwise from
+                                    local East, rad */
+    int upsample;                /* U of the FFT upsample, 1..8 (2 recommended) */
+    double sigma2;               /* noise variance; <= 0: (1/N) sum x^2 per band */
+    fstat_form form;
+    int64_t cand_capacity;       /* device candidate records kept per search, >= 1 */
+    void *cuda_stream;           /* cudaStream_t to run on, or NULL (the plan's own) */
+    int inputs_on_device;        /* 0: x/x32/r/alpha/delta/fdot are host pointers;
+                                    1: they are device pointers (copied device->device) */
+} fstat_plan_desc;
+
+/* One registered candidate (Sect. 2: sky position, frequency, spindown, F),
+   plus the integer grid indices that identify it exactly. */
+typedef struct {
+    double alpha, delta;   /* sky position, rad */
+    double freq;           /* f_off + bin / (n_fft dt), Hz */
+    double fdot;           /* Hz/s */
+    double F;              /* the F-statistic (not 2F) */
+    int32_t band;
+    int32_t reserved;
+    int64_t sky, spin, bin;
+} fstat_candidate;
+
+typedef struct {
+    int64_t n_cells;         /* n_bands * n_sky * n_spin */
+    int64_t f_evals;         /* cells x searched bins, summed over bands */
+    int64_t device_bytes;    /* device memory the plan holds */
+    int64_t kernel_launches; /* kernels launched by the plan so far (graph nodes count) */
+    int64_t n_fft_max;
+} fstat_plan_info;
+
+typedef struct fstat_plan fstat_plan;
+
+/* Validate the description, allocate device memory, copy the inputs and prepare
+   the launch configuration.  On success *out receives a plan; on failure *out is
+   NULL and nothing is leaked.  Errors: FSTAT_ERR_ARG (any field out of range,
+   NULL where a pointer is required, x and x32 both or neither given, more than
+   2^32 - 1 cells), FSTAT_ERR_OOM, FSTAT_ERR_CUDA. */
+fstat_status fstat_plan_create(fstat_plan **out, const fstat_plan_desc *desc);
+
+/* Search cells [cell_begin, cell_end) in the order cell = (band * n_sky + sky)
+   * n_spin + spin (cell_end = -1: to the last cell), replacing the candidates of
+   the previous call.  Runs the whole hot path from the raw series: per band the
+   noise variance and the FFT upsample; per sky the delay, a(t), b(t), the
+   resampled and phase-demodulated series and S_aa, S_bb; per cell the spindown
+   demodulation, the two zero-padded FFTs, F per bin, the threshold and the
+   compaction of candidates into device memory.  Returns FSTAT_ERR_OVERFLOW when
+   more than cand_capacity candidates were found (the first cand_capacity found
+   are kept; the total stays exact). */
+fstat_status fstat_search(fstat_plan *plan, int64_t cell_begin, int64_t cell_end);
+
+/* Copy the candidates of the last search into buf[0 .. cap), sorted by
+   (band, sky, spin, bin).  *n_written = min(kept, cap); *n_total = every
+   candidate found, including those beyond the device capacity.  Returns
+   FSTAT_ERR_OVERFLOW when *n_total > *n_written.  buf may be NULL when cap = 0. */
+fstat_status fstat_candidates_get(fstat_plan *plan, fstat_candidate *buf, int64_t cap,
+                                  int64_t *n_written, int64_t *n_total);
+
+/* Diagnostics of the per-sky stage (geometry, resampling, phase demodulation)
+   for one (band, sky) of the plan's inputs, as the search computes it: y[2n]
+   interleaved complex resampled series, a[n], b[n], mask[n] (1 inside the
+   resampled window), S[3] = {S_aa, S_bb, S_ab}.  Host pointers; any may be NULL.
+   FP32_BATCHED plans report their FP32 values widened to double. */
+fstat_status fstat_debug_sky(fstat_plan *plan, int band, int64_t sky, double *y, double *a,
+                             double *b, uint8_t *mask, double *S);
+
+fstat_status fstat_plan_get_info(const fstat_plan *plan, fstat_plan_info *info);
+
+/* Per-kernel timing, measured with CUDA events on the plan's stream while it
+   searches.  With sample_every = k > 0, every k-th launch of each timed kernel
+   class is bracketed by events (the others run untouched), so the averages
+   describe the launches of a normal search; k = 0 switches timing off.
+   fstat_plan_kernel_stats fills up to cap entries (one per kernel class seen
+   since timing was switched on) and returns their number in *n. */
+typedef struct {
+    char name[32];
+    int64_t launches;        /* launches of this class since timing was switched on */
+    int64_t timed_launches;  /* of which bracketed by events */
+    double timed_ms;         /* summed duration of the timed launches */
+    double flops_per_launch; /* algorithmic FP32/FP64 operations of one launch (mean) */
+    double bytes_per_launch; /* algorithmic DRAM bytes of one launch (mean) */
+} fstat_kernel_stat;
+
+fstat_status fstat_plan_set_timing(fstat_plan *plan, int sample_every);
+fstat_status fstat_plan_kernel_stats(const fstat_plan *plan, fstat_kernel_stat *out, int cap,
+                                     int *n);
+
+/* Release everything the plan holds.  NULL is accepted. */
+void fstat_plan_destroy(fstat_plan *plan);
+
+/* Static description of a status code. */
+const char *fstat_status_string(fstat_status s);
+
+/* Last error message of this plan ("" when none); valid until the next call. */
+const char *fstat_plan_error(const fstat_plan *plan);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,645 @@
+// Host side of libfstat.so: argument validation, device memory, the order of
+// launches of one search, candidate retrieval.  See include/fstat.h.
+#include <math.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "fstat_internal.h"
+
+struct fstat_plan : public fstat::Plan {};
+
+namespace fstat {
+
+namespace {
+
+constexpr double kTwoPi = 6.283185307179586476925286766559;
+
+struct CudaError {
+    cudaError_t e;
+    const char *what;
+};
+
+// Test hook: FSTAT_TEST_FAIL_ALLOC=k makes the k-th device allocation of a plan
+// (1-based) report failure, to exercise the out-of-memory path on the host.
+int alloc_fail_at() {
+    const char *v = getenv("FSTAT_TEST_FAIL_ALLOC");
+    return v ? atoi(v) : 0;
+}
+
+void check(cudaError_t e, const char *what) {
+    if (e != cudaSuccess) throw CudaError{e, what};
+}
+
+struct OomError {};
+
+template <typename T>
+T *dalloc(Plan &p, size_t count, int &n_alloc) {
+    ++n_alloc;
+    const int fail = alloc_fail_at();
+    if (fail > 0 && n_alloc == fail) throw OomError{};
+    void *ptr = nullptr;
+    const size_t bytes = std::max<size_t>(count * sizeof(T), 16);
+    cudaError_t e = cudaMalloc(&ptr, bytes);
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();
+        throw OomError{};
+    }
+    check(e, "cudaMalloc");
+    p.allocs.push_back(ptr);
+    p.device_bytes += (int64_t)bytes;
+    return reinterpret_cast<T *>(ptr);
+}
+
+int ilog2_exact(int64_t v) {
+    int l = 0;
+    while ((int64_t(1) << l) < v) ++l;
+    return ((int64_t(1) << l) == v) ? l : -1;
+}
+
+bool is_finite(double v) { return isfinite(v) != 0; }
+
+// Fixed-point 2^-64 cycles of frac(rate): exact wrap-around arithmetic on device.
+uint64_t to_fixed64(double rate) {
+    double fr = rate - floor(rate);          // [0, 1)
+    double hi = floor(fr * 4294967296.0);    // top 32 bits
+    double lo = (fr * 4294967296.0 - hi) * 4294967296.0;
+    uint64_t h = (uint64_t)hi, l = (uint64_t)llround(lo);
+    return (h << 32) + l;                    // l may round to 2^32: carries into h
+}
+
+std::string band_err(int i, const char *m) { return "band " + std::to_string(i) + ": " + m; }
+
+fstat_status validate(const fstat_plan_desc *d, std::string &err) {
+    if (!d) { err = "desc is NULL"; return FSTAT_ERR_ARG; }
+    if (d->n_bands < 1 || !d->bands) { err = "need n_bands >= 1 and bands"; return FSTAT_ERR_ARG; }
+    if (d->n_sky < 1 || !d->alpha || !d->delta) { err = "need n_sky >= 1, alpha, delta"; return FSTAT_ERR_ARG; }
+    if (d->n_spin < 1 || !d->fdot) { err = "need n_spin >= 1 and fdot"; return FSTAT_ERR_ARG; }
+    if (d->form != FSTAT_FP64_PLAIN && d->form != FSTAT_FP32_BATCHED) { err = "unknown form"; return FSTAT_ERR_ARG; }
+    if (d->upsample < 1 || d->upsample > 8) { err = "upsample must be 1..8"; return FSTAT_ERR_ARG; }
+    if (d->cand_capacity < 1 || d->cand_capacity > (int64_t(1) << 34)) { err = "cand_capacity out of range"; return FSTAT_ERR_ARG; }
+    if (!is_finite(d->thr_2F) || !is_finite(d->lat) || !is_finite(d->gamma) || !is_finite(d->sigma2)) {
+        err = "non-finite scalar"; return FSTAT_ERR_ARG;
+    }
+    if (d->inputs_on_device != 0 && d->inputs_on_device != 1) { err = "inputs_on_device must be 0 or 1"; return FSTAT_ERR_ARG; }
+    const int64_t cells = (int64_t)d->n_bands * d->n_sky * d->n_spin;
+    if (d->n_sky > (int64_t(1) << 31) || d->n_spin > (int64_t(1) << 31) || cells >= (int64_t(1) << 32)) {
+        err = "more than 2^32 - 1 cells"; return FSTAT_ERR_ARG;
+    }
+    for (int i = 0; i < d->n_bands; ++i) {
+        const fstat_band &b = d->bands[i];
+        if (b.n < 16 || b.n > (int64_t(1) << 19)) { err = band_err(i, "n must be 16 .. 2^19"); return FSTAT_ERR_ARG; }
+        if (!(b.dt > 0) || !is_finite(b.dt) || !is_finite(b.f_off) || !is_finite(b.phi0)) { err = band_err(i, "bad dt/f_off/phi0"); return FSTAT_ERR_ARG; }
+        if ((b.x == nullptr) == (b.x32 == nullptr)) { err = band_err(i, "give exactly one of x, x32"); return FSTAT_ERR_ARG; }
+        if (!b.r) { err = band_err(i, "r is NULL"); return FSTAT_ERR_ARG; }
+        int64_t nf = b.n_fft;
+        if (nf == 0) { nf = 1; while (nf < 2 * b.n) nf <<= 1; }
+        const int lg = ilog2_exact(nf);
+        if (lg < kMinLogN || lg > kMaxLogN || nf < 2 * b.n) { err = band_err(i, "n_fft must be a power of two >= 2n in [256, 2^20]"); return FSTAT_ERR_ARG; }
+        if (d->bin_lo != 0 || d->bin_hi != 0) {
+            if (d->bin_lo < 0 || d->bin_hi < d->bin_lo || d->bin_hi >= nf) { err = band_err(i, "bin range outside [0, n_fft)"); return FSTAT_ERR_ARG; }
+        }
+    }
+    return FSTAT_OK;
+}
+
+void host_twiddles(int logn, std::vector<double> &in1, std::vector<double> &in2,
+                   std::vector<double> &lo, std::vector<double> &hi) {
+    const int64_t N = int64_t(1) << logn;
+    const int64_t N1 = int64_t(1) << log_n1(logn), N2 = int64_t(1) << log_n2(logn);
+    auto w = [](int64_t k, int64_t M, double *o) {
+        // e^{-2 pi i k / M} with k reduced to the first octant-free form
+        const double a = -kTwoPi * (double)k / (double)M;
+        o[0] = cos(a);
+        o[1] = sin(a);
+    };
+    in1.resize(2 * N1); in2.resize(2 * N2); lo.resize(2 * N1); hi.resize(2 * N2);
+    for (int64_t k = 0; k < N1; ++k) w(k, N1, &in1[2 * k]);
+    for (int64_t k = 0; k < N2; ++k) w(k, N2, &in2[2 * k]);
+    for (int64_t k = 0; k < N1; ++k) w(k, N, &lo[2 * k]);
+    for (int64_t k = 0; k < N2; ++k) w(k * N1, N, &hi[2 * k]);
+}
+
+void build_twiddles(Plan &p, const std::vector<int> &logs, int &n_alloc) {
+    std::vector<double> hd;
+    std::vector<size_t> offs;
+    for (int lg : logs) {
+        std::vector<double> a, b, c, d;
+        host_twiddles(lg, a, b, c, d);
+        for (auto *v : {&a, &b, &c, &d}) {
+            offs.push_back(hd.size());
+            hd.insert(hd.end(), v->begin(), v->end());
+        }
+    }
+    double *dd = dalloc<double>(p, hd.size(), n_alloc);
+    float *df = dalloc<float>(p, hd.size(), n_alloc);
+    std::vector<float> hf(hd.begin(), hd.end());
+    check(cudaMemcpy(dd, hd.data(), hd.size() * sizeof(double), cudaMemcpyHostToDevice), "twiddles");
+    check(cudaMemcpy(df, hf.data(), hf.size() * sizeof(float), cudaMemcpyHostToDevice), "twiddles");
+    for (size_t i = 0; i < logs.size(); ++i) {
+        TwiddleSet t;
+        t.logn = logs[i];
+        t.in1_d = dd + offs[4 * i]; t.in2_d = dd + offs[4 * i + 1];
+        t.lo_d = dd + offs[4 * i + 2]; t.hi_d = dd + offs[4 * i + 3];
+        t.in1_f = df + offs[4 * i]; t.in2_f = df + offs[4 * i + 1];
+        t.lo_f = df + offs[4 * i + 2]; t.hi_f = df + offs[4 * i + 3];
+        p.tw.push_back(t);
+    }
+}
+
+__global__ void k_f32_to_f64(const float *__restrict__ in, int64_t n, double *__restrict__ out) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) out[i] = (double)in[i];
+}
+
+void copy_in(void *dst, const void *src, size_t bytes, bool on_device, cudaStream_t s) {
+    check(cudaMemcpyAsync(dst, src, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s),
+          "input copy");
+}
+
+void create_impl(Plan &p, const fstat_plan_desc *d) {
+    int n_alloc = 0;
+    p.desc = *d;
+    const bool dev = d->inputs_on_device == 1;
+    const bool fp32 = d->form == FSTAT_FP32_BATCHED;
+    if (d->cuda_stream) {
+        p.stream = (cudaStream_t)d->cuda_stream;
+    } else {
+        check(cudaStreamCreateWithFlags(&p.stream, cudaStreamNonBlocking), "cudaStreamCreate");
+        p.own_stream = true;
+    }
+    cudaStream_t s = p.stream;
+    const int U = d->upsample;
+
+    // grids (host copies kept for candidate retrieval and the chirp tables)
+    p.h_alpha.resize(d->n_sky); p.h_delta.resize(d->n_sky); p.h_fdot.resize(d->n_spin);
+    const cudaMemcpyKind k2h = dev ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost;
+    check(cudaMemcpy(p.h_alpha.data(), d->alpha, d->n_sky * sizeof(double), k2h), "alpha");
+    check(cudaMemcpy(p.h_delta.data(), d->delta, d->n_sky * sizeof(double), k2h), "delta");
+    check(cudaMemcpy(p.h_fdot.data(), d->fdot, d->n_spin * sizeof(double), k2h), "fdot");
+    for (int64_t i = 0; i < d->n_sky; ++i)
+        if (!is_finite(p.h_alpha[i]) || !is_finite(p.h_delta[i])) throw std::string("non-finite sky position");
+    for (int64_t j = 0; j < d->n_spin; ++j)
+        if (!is_finite(p.h_fdot[j])) throw std::string("non-finite spindown");
+
+    std::vector<int> logs;
+    auto need = [&](int lg) { if (std::find(logs.begin(), logs.end(), lg) == logs.end()) logs.push_back(lg); };
+    int64_t max_m = 0, max_nfft = 0;
+    p.n_max = 0;
+    for (int i = 0; i < d->n_bands; ++i) {
+        const fstat_band &hb = d->bands[i];
+        BandDev b;
+        b.n = hb.n; b.dt = hb.dt; b.f_off = hb.f_off; b.phi0 = hb.phi0; b.eps = hb.eps;
+        b.n_fft = hb.n_fft;
+        if (b.n_fft == 0) { b.n_fft = 1; while (b.n_fft < 2 * b.n) b.n_fft <<= 1; }
+        b.logn = ilog2_exact(b.n_fft);
+        need(b.logn);
+        if (d->bin_lo == 0 && d->bin_hi == 0) { b.lo = 1; b.hi = b.n_fft / 2 - 1; }
+        else { b.lo = d->bin_lo; b.hi = d->bin_hi; }
+        // upsample transforms: a power of two >= 256 directly, else Bluestein
+        if (U > 1) {
+            const int lgn = ilog2_exact(b.n);
+            if (lgn >= kMinLogN && lgn <= kMaxLogN) need(lgn);
+            else {
+                int lm = kMinLogN;
+                while ((int64_t(1) << lm) < 2 * b.n - 1) ++lm;
+                need(lm);
+                max_m = std::max<int64_t>(max_m, int64_t(1) << lm);
+            }
+        }
+        max_nfft = std::max(max_nfft, b.n_fft);
+        p.n_max = std::max(p.n_max, b.n);
+        b.x = dalloc<double>(p, b.n, n_alloc);
+        b.r = dalloc<double>(p, 3 * b.n, n_alloc);
+        b.sigma2 = dalloc<double>(p, 1, n_alloc);
+        b.xu = fp32 ? (void *)dalloc<float>(p, (size_t)U * b.n, n_alloc)
+                    : (void *)dalloc<double>(p, (size_t)U * b.n, n_alloc);
+        if (hb.x) {
+            copy_in(b.x, hb.x, b.n * sizeof(double), dev, s);
+        } else {
+            float *tmp = dalloc<float>(p, b.n, n_alloc);
+            copy_in(tmp, hb.x32, b.n * sizeof(float), dev, s);
+            k_f32_to_f64<<<(unsigned)((b.n + 255) / 256), 256, 0, s>>>(tmp, b.n, b.x);
+            ++p.launches;
+        }
+        copy_in(b.r, hb.r, 3 * b.n * sizeof(double), dev, s);
+        p.bands.push_back(b);
+        p.n_cells += d->n_sky * d->n_spin;
+        p.f_evals += d->n_sky * d->n_spin * (b.hi - b.lo + 1);
+    }
+    p.n_fft_max = max_nfft;
+    build_twiddles(p, logs, n_alloc);
+
+    p.alpha = dalloc<double>(p, d->n_sky, n_alloc);
+    p.delta = dalloc<double>(p, d->n_sky, n_alloc);
+    p.fdot = dalloc<double>(p, d->n_spin, n_alloc);
+    check(cudaMemcpyAsync(p.alpha, p.h_alpha.data(), d->n_sky * sizeof(double), cudaMemcpyHostToDevice, s), "alpha");
+    check(cudaMemcpyAsync(p.delta, p.h_delta.data(), d->n_sky * sizeof(double), cudaMemcpyHostToDevice, s), "delta");
+    check(cudaMemcpyAsync(p.fdot, p.h_fdot.data(), d->n_spin * sizeof(double), cudaMemcpyHostToDevice, s), "fdot");
+    p.sky = dalloc<SkyConst>(p, d->n_sky, n_alloc);
+    p.launches += launch_sky_consts(p.alpha, p.delta, d->n_sky, d->lat, d->gamma, p.sky, s);
+
+    // spindown phase rates per (band, spin): fdot dt^2 / 2 cycles per k^2
+    std::vector<uint64_t> cfx((size_t)d->n_bands * d->n_spin);
+    std::vector<double> cd((size_t)d->n_bands * d->n_spin);
+    for (int i = 0; i < d->n_bands; ++i)
+        for (int64_t j = 0; j < d->n_spin; ++j) {
+            const double rate = 0.5 * p.h_fdot[j] * d->bands[i].dt * d->bands[i].dt;
+            cd[(size_t)i * d->n_spin + j] = rate;
+            cfx[(size_t)i * d->n_spin + j] = to_fixed64(rate);
+        }
+    p.chirp_fx = dalloc<uint64_t>(p, cfx.size(), n_alloc);
+    p.chirp_d = dalloc<double>(p, cd.size(), n_alloc);
+    check(cudaMemcpy(p.chirp_fx, cfx.data(), cfx.size() * sizeof(uint64_t), cudaMemcpyHostToDevice), "chirp");
+    check(cudaMemcpy(p.chirp_d, cd.data(), cd.size() * sizeof(double), cudaMemcpyHostToDevice), "chirp");
+
+    // per-sky-batch buffers
+    const int64_t nblk = (p.n_max + 255) / 256;
+    p.sky_batch = fp32 ? std::min<int64_t>(d->n_sky, 64) : 1;
+    const size_t w_elem = fp32 ? 16 : 32;
+    p.w = dalloc<unsigned char>(p, (size_t)p.sky_batch * p.n_max * w_elem, n_alloc);
+    p.partials = dalloc<double>(p, std::max<int64_t>((int64_t)p.sky_batch * nblk * 3, 256), n_alloc);
+    p.S = dalloc<double>(p, 3 * p.sky_batch, n_alloc);
+    p.norm = dalloc<double>(p, 2 * p.sky_batch, n_alloc);
+
+    // FFT scratch: cell slots of 2 transforms; also hosts the generic FFT of the upsample
+    const size_t tsz = fp32 ? sizeof(float2) : sizeof(double2);
+    if (fp32) {
+        const int64_t budget = int64_t(64) << 20;
+        p.cell_batch = std::max<int64_t>(1, std::min<int64_t>(4096, budget / (2 * max_nfft * (int64_t)tsz)));
+    } else {
+        p.cell_batch = 1;
+    }
+    const size_t scratch_bytes = std::max<size_t>((size_t)p.cell_batch * 2 * max_nfft * tsz,
+                                                  (size_t)2 * std::max<int64_t>(max_m, p.n_max) * sizeof(double2) * 2);
+    p.scratch = dalloc<unsigned char>(p, scratch_bytes, n_alloc);
+    p.bw_elems = 2 * p.n_max + 2 * max_m;
+    p.bw = dalloc<double>(p, 2 * (size_t)std::max<int64_t>(p.bw_elems, 1), n_alloc);
+
+    p.cand_capacity = d->cand_capacity;
+    p.cand = dalloc<CandRecord>(p, (size_t)p.cand_capacity, n_alloc);
+    p.cand_count = dalloc<unsigned long long>(p, 1, n_alloc);
+    check(cudaMemsetAsync(p.cand_count, 0, sizeof(unsigned long long), s), "memset");
+    check(cudaStreamSynchronize(s), "plan setup");
+    check(cudaGetLastError(), "plan setup launch");
+}
+
+void free_all(Plan &p) {
+    if (!p.allocs.empty() || p.own_stream) cudaDeviceSynchronize();
+    for (void *ptr : p.allocs) cudaFree(ptr);
+    p.allocs.clear();
+    for (cudaEvent_t e : p.ev_all) cudaEventDestroy(e);
+    p.ev_all.clear();
+    p.ev_pool.clear();
+    p.pending.clear();
+    if (p.own_stream && p.stream) cudaStreamDestroy(p.stream);
+    p.stream = nullptr;
+    p.own_stream = false;
+}
+
+// ---------------------------------------------------------------- sampled timing
+int stat_index(Plan &p, const char *name) {
+    for (size_t i = 0; i < p.kstats.size(); ++i)
+        if (p.kstats[i].name == name) return (int)i;
+    Plan::KStat k;
+    k.name = name;
+    p.kstats.push_back(k);
+    return (int)p.kstats.size() - 1;
+}
+
+cudaEvent_t ev_get(Plan &p) {
+    if (!p.ev_pool.empty()) {
+        cudaEvent_t e = p.ev_pool.back();
+        p.ev_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e;
+    check(cudaEventCreate(&e), "cudaEventCreate");
+    p.ev_all.push_back(e);
+    return e;
+}
+
+// Counts one launch of class `name` with its algorithmic work; returns whether
+// this launch is one of the sampled ones.
+bool stat_launch(Plan &p, int idx, double flops, double bytes) {
+    auto &k = p.kstats[(size_t)idx];
+    k.launches += 1;
+    k.flops += flops;
+    k.bytes += bytes;
+    return p.timing_every > 0 && (k.launches - 1) % p.timing_every == 0;
+}
+
+void collect_timing(Plan &p) {
+    for (auto &pe : p.pending) {
+        float ms = 0.f;
+        check(cudaEventElapsedTime(&ms, pe.a, pe.b), "cudaEventElapsedTime");
+        p.kstats[(size_t)pe.stat].timed += 1;
+        p.kstats[(size_t)pe.stat].ms += ms;
+        p.ev_pool.push_back(pe.a);
+        p.ev_pool.push_back(pe.b);
+    }
+    p.pending.clear();
+}
+
+// Per-band prologue: sigma^2 and the FFT upsample.
+void band_prologue(Plan &p, BandDev &b) {
+    const bool fp32 = p.desc.form == FSTAT_FP32_BATCHED;
+    const int idx = stat_index(p, "band_prologue");
+    const bool t = stat_launch(p, idx, 0.0, (double)b.n * 8.0 * (1 + p.desc.upsample));
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (t) { e0 = ev_get(p); e1 = ev_get(p); check(cudaEventRecord(e0, p.stream), "event"); }
+    p.launches += launch_sigma2(b.x, b.n, p.desc.sigma2, p.partials, b.sigma2, p.stream);
+    p.launches += launch_upsample(p, b, p.desc.upsample, b.xu, fp32, p.stream);
+    if (t) { check(cudaEventRecord(e1, p.stream), "event"); p.pending.push_back({idx, e0, e1}); }
+}
+
+void search_impl(Plan &p, int64_t begin, int64_t end) {
+    const fstat_plan_desc &d = p.desc;
+    const bool fp32 = d.form == FSTAT_FP32_BATCHED;
+    cudaStream_t s = p.stream;
+    check(cudaMemsetAsync(p.cand_count, 0, sizeof(unsigned long long), s), "memset");
+    const int64_t per_band = d.n_sky * d.n_spin;
+    for (int bi = 0; bi < d.n_bands; ++bi) {
+        const int64_t b0 = (int64_t)bi * per_band;
+        const int64_t lc0 = std::max<int64_t>(begin, b0) - b0;
+        const int64_t lc1 = std::min<int64_t>(end, b0 + per_band) - b0;
+        if (lc1 <= lc0) continue;
+        BandDev &b = p.bands[bi];
+        band_prologue(p, b);
+        const int64_t s_first = lc0 / d.n_spin, s_last = (lc1 - 1) / d.n_spin;
+        const double nfft = (double)b.n_fft;
+        const double lg1 = (double)log_n1(b.logn), lg2 = (double)log_n2(b.logn);
+        const int i_geo = stat_index(p, "geometry_resample");
+        const int i_p1 = stat_index(p, fp32 ? "fft_pass1_f32" : "fft_pass1_f64");
+        const int i_p2 = stat_index(p, fp32 ? "fft_pass2_fstat_f32" : "fft_pass2_fstat_f64");
+        const double welem = fp32 ? 16.0 : 32.0;
+        for (int64_t sb = s_first; sb <= s_last; sb += p.sky_batch) {
+            const int64_t ns = std::min<int64_t>(p.sky_batch, s_last + 1 - sb);
+            // algorithmic bytes: ephemeris + upsampled series read, w written per sky
+            const bool tg = stat_launch(p, i_geo, 0.0,
+                                        (double)b.n * (24.0 + welem * ns) + (double)p.desc.upsample * b.n * (fp32 ? 4 : 8));
+            cudaEvent_t g0 = nullptr, g1 = nullptr;
+            if (tg) { g0 = ev_get(p); g1 = ev_get(p); check(cudaEventRecord(g0, s), "event"); }
+            p.launches += launch_geometry(p, b, sb, ns, fp32, nullptr, nullptr, nullptr, nullptr, s);
+            p.launches += launch_reduce_norms(p, b, ns, s);
+            if (tg) { check(cudaEventRecord(g1, s), "event"); p.pending.push_back({i_geo, g0, g1}); }
+            const int64_t c_lo = std::max<int64_t>(lc0, sb * d.n_spin);
+            const int64_t c_hi = std::min<int64_t>(lc1, (sb + ns) * d.n_spin);
+            for (int64_t c = c_lo; c < c_hi; c += p.cell_batch) {
+                const int64_t nc = std::min<int64_t>(p.cell_batch, c_hi - c);
+                // 5 N log2 N per complex transform, split between the passes; two
+                // transforms per cell.  Pass 1 reads w once per distinct sky.
+                const int64_t sky_a = c / d.n_spin, sky_b = (c + nc - 1) / d.n_spin;
+                const bool t1 = stat_launch(p, i_p1, 2.0 * nc * 5.0 * nfft * lg2,
+                                            (double)(sky_b - sky_a + 1) * b.n * welem);
+                stat_launch(p, i_p2, 2.0 * nc * 5.0 * nfft * lg1, 0.0);
+                cudaEvent_t e0 = nullptr, e1 = nullptr, e2 = nullptr;
+                if (t1) {
+                    e0 = ev_get(p); e1 = ev_get(p); e2 = ev_get(p);
+                    check(cudaEventRecord(e0, s), "event");
+                }
+                const int L = fp32 ? launch_search_cells_f32(p, bi, b, sb, c, nc, s, e1)
+                                   : launch_search_cells_f64(p, bi, b, sb, c, nc, s, e1);
+                if (L < 0) throw std::string("unsupported transform length");
+                p.launches += L;
+                if (t1) {
+                    check(cudaEventRecord(e2, s), "event");
+                    p.pending.push_back({i_p1, e0, e1});
+                    p.pending.push_back({i_p2, e1, e2});
+                }
+            }
+        }
+    }
+    check(cudaGetLastError(), "search launch");
+    check(cudaStreamSynchronize(s), "search");
+    collect_timing(p);
+    unsigned long long cnt = 0;
+    check(cudaMemcpy(&cnt, p.cand_count, sizeof(cnt), cudaMemcpyDeviceToHost), "count");
+    p.last_total = (int64_t)cnt;
+    p.searched = true;
+}
+
+template <class F>
+fstat_status guarded(fstat_plan *p, F &&f) {
+    if (!p) return FSTAT_ERR_ARG;
+    if (p->poisoned) return FSTAT_ERR_STATE;
+    p->err.clear();
+    try {
+        return f();
+    } catch (const CudaError &e) {
+        p->err = std::string(e.what) + ": " + cudaGetErrorString(e.e);
+        p->poisoned = true;
+        return FSTAT_ERR_CUDA;
+    } catch (const OomError &) {
+        p->err = "out of device memory";
+        return FSTAT_ERR_OOM;
+    } catch (const std::bad_alloc &) {
+        p->err = "out of host memory";
+        return FSTAT_ERR_OOM;
+    } catch (const std::string &m) {
+        p->err = m;
+        return FSTAT_ERR_ARG;
+    }
+}
+
+}  // namespace
+}  // namespace fstat
+
+using namespace fstat;
+
+extern "C" {
+
+fstat_status fstat_plan_create(fstat_plan **out, const fstat_plan_desc *desc) {
+    if (!out) return FSTAT_ERR_ARG;
+    *out = nullptr;
+    std::string err;
+    fstat_status st = validate(desc, err);
+    if (st != FSTAT_OK) {
+        if (getenv("FSTAT_LOG")) fprintf(stderr, "fstat_plan_create: %s\n", err.c_str());
+        return st;
+    }
+    fstat_plan *p = new (std::nothrow) fstat_plan();
+    if (!p) return FSTAT_ERR_OOM;
+    try {
+        create_impl(*p, desc);
+    } catch (const CudaError &e) {
+        if (getenv("FSTAT_LOG")) fprintf(stderr, "fstat_plan_create: %s: %s\n", e.what, cudaGetErrorString(e.e));
+        free_all(*p);
+        delete p;
+        return FSTAT_ERR_CUDA;
+    } catch (const OomError &) {
+        free_all(*p);
+        delete p;
+        return FSTAT_ERR_OOM;
+    } catch (const std::bad_alloc &) {
+        free_all(*p);
+        delete p;
+        return FSTAT_ERR_OOM;
+    } catch (const std::string &m) {
+        if (getenv("FSTAT_LOG")) fprintf(stderr, "fstat_plan_create: %s\n", m.c_str());
+        free_all(*p);
+        delete p;
+        return FSTAT_ERR_ARG;
+    }
+    *out = p;
+    return FSTAT_OK;
+}
+
+fstat_status fstat_search(fstat_plan *p, int64_t cell_begin, int64_t cell_end) {
+    return guarded(p, [&]() -> fstat_status {
+        if (cell_end < 0) cell_end = p->n_cells;
+        if (cell_begin < 0 || cell_begin > cell_end || cell_end > p->n_cells) {
+            p->err = "cell range outside [0, n_cells]";
+            return FSTAT_ERR_ARG;
+        }
+        search_impl(*p, cell_begin, cell_end);
+        return p->last_total > p->cand_capacity ? FSTAT_ERR_OVERFLOW : FSTAT_OK;
+    });
+}
+
+fstat_status fstat_candidates_get(fstat_plan *p, fstat_candidate *buf, int64_t cap,
+                                  int64_t *n_written, int64_t *n_total) {
+    return guarded(p, [&]() -> fstat_status {
+        if (cap < 0 || (cap > 0 && !buf)) { p->err = "bad buffer"; return FSTAT_ERR_ARG; }
+        if (n_written) *n_written = 0;
+        if (n_total) *n_total = 0;
+        if (!p->searched) return FSTAT_OK;
+        const int64_t kept = std::min<int64_t>(p->last_total, p->cand_capacity);
+        std::vector<CandRecord> rec((size_t)kept);
+        if (kept > 0)
+            check(cudaMemcpy(rec.data(), p->cand, kept * sizeof(CandRecord), cudaMemcpyDeviceToHost), "candidates");
+        std::sort(rec.begin(), rec.end(), [](const CandRecord &a, const CandRecord &b) {
+            return a.cell != b.cell ? a.cell < b.cell : a.bin < b.bin;
+        });
+        const int64_t nw = std::min<int64_t>(kept, cap);
+        const fstat_plan_desc &d = p->desc;
+        for (int64_t i = 0; i < nw; ++i) {
+            const CandRecord &r = rec[(size_t)i];
+            const int64_t per_band = d.n_sky * d.n_spin;
+            const int band = (int)(r.cell / per_band);
+            const int64_t rem = r.cell - (int64_t)band * per_band;
+            fstat_candidate &c = buf[i];
+            c.band = band;
+            c.reserved = 0;
+            c.sky = rem / d.n_spin;
+            c.spin = rem % d.n_spin;
+            c.bin = r.bin;
+            c.alpha = p->h_alpha[(size_t)c.sky];
+            c.delta = p->h_delta[(size_t)c.sky];
+            c.fdot = p->h_fdot[(size_t)c.spin];
+            const BandDev &b = p->bands[(size_t)band];
+            c.freq = b.f_off + (double)r.bin / ((double)b.n_fft * b.dt);
+            c.F = r.F;
+        }
+        if (n_written) *n_written = nw;
+        if (n_total) *n_total = p->last_total;
+        return p->last_total > nw ? FSTAT_ERR_OVERFLOW : FSTAT_OK;
+    });
+}
+
+fstat_status fstat_debug_sky(fstat_plan *p, int band, int64_t sky, double *y, double *a,
+                             double *b, uint8_t *mask, double *S) {
+    return guarded(p, [&]() -> fstat_status {
+        if (band < 0 || band >= p->desc.n_bands || sky < 0 || sky >= p->desc.n_sky) {
+            p->err = "band or sky out of range";
+            return FSTAT_ERR_ARG;
+        }
+        BandDev &bd = p->bands[(size_t)band];
+        const int64_t n = bd.n;
+        double *dy = nullptr, *da = nullptr, *db = nullptr;
+        uint8_t *dm = nullptr;
+        int n_alloc = 0;
+        const size_t before = p->allocs.size();
+        const int64_t bytes_before = p->device_bytes;
+        try {
+            dy = dalloc<double>(*p, 2 * n, n_alloc);
+            da = dalloc<double>(*p, n, n_alloc);
+            db = dalloc<double>(*p, n, n_alloc);
+            dm = dalloc<uint8_t>(*p, n, n_alloc);
+        } catch (...) {
+            for (size_t i = before; i < p->allocs.size(); ++i) cudaFree(p->allocs[i]);
+            p->allocs.resize(before);
+            p->device_bytes = bytes_before;
+            throw;
+        }
+        const bool fp32 = p->desc.form == FSTAT_FP32_BATCHED;
+        band_prologue(*p, bd);
+        p->launches += launch_geometry(*p, bd, sky, 1, fp32, dy, da, db, dm, p->stream);
+        p->launches += launch_reduce_norms(*p, bd, 1, p->stream);
+        check(cudaStreamSynchronize(p->stream), "debug sky");
+        if (y) check(cudaMemcpy(y, dy, 2 * n * sizeof(double), cudaMemcpyDeviceToHost), "y");
+        if (a) check(cudaMemcpy(a, da, n * sizeof(double), cudaMemcpyDeviceToHost), "a");
+        if (b) check(cudaMemcpy(b, db, n * sizeof(double), cudaMemcpyDeviceToHost), "b");
+        if (mask) check(cudaMemcpy(mask, dm, n, cudaMemcpyDeviceToHost), "mask");
+        if (S) check(cudaMemcpy(S, p->S, 3 * sizeof(double), cudaMemcpyDeviceToHost), "S");
+        for (size_t i = before; i < p->allocs.size(); ++i) cudaFree(p->allocs[i]);
+        p->allocs.resize(before);
+        p->device_bytes = bytes_before;
+        return FSTAT_OK;
+    });
+}
+
+fstat_status fstat_plan_set_timing(fstat_plan *p, int sample_every) {
+    return guarded(p, [&]() -> fstat_status {
+        if (sample_every < 0) { p->err = "sample_every must be >= 0"; return FSTAT_ERR_ARG; }
+        p->timing_every = sample_every;
+        p->kstats.clear();
+        return FSTAT_OK;
+    });
+}
+
+fstat_status fstat_plan_kernel_stats(const fstat_plan *p, fstat_kernel_stat *out, int cap, int *n) {
+    if (!p || !n || cap < 0 || (cap > 0 && !out)) return FSTAT_ERR_ARG;
+    const int m = std::min<int>(cap, (int)p->kstats.size());
+    for (int i = 0; i < m; ++i) {
+        const auto &k = p->kstats[(size_t)i];
+        memset(&out[i], 0, sizeof(fstat_kernel_stat));
+        strncpy(out[i].name, k.name.c_str(), sizeof(out[i].name) - 1);
+        out[i].launches = k.launches;
+        out[i].timed_launches = k.timed;
+        out[i].timed_ms = k.ms;
+        out[i].flops_per_launch = k.launches ? k.flops / (double)k.launches : 0.0;
+        out[i].bytes_per_launch = k.launches ? k.bytes / (double)k.launches : 0.0;
+    }
+    *n = (int)p->kstats.size();
+    return FSTAT_OK;
+}
+
+fstat_status fstat_plan_get_info(const fstat_plan *p, fstat_plan_info *info) {
+    if (!p || !info) return FSTAT_ERR_ARG;
+    info->n_cells = p->n_cells;
+    info->f_evals = p->f_evals;
+    info->device_bytes = p->device_bytes;
+    info->kernel_launches = p->launches;
+    info->n_fft_max = p->n_fft_max;
+    return FSTAT_OK;
+}
+
+void fstat_plan_destroy(fstat_plan *p) {
+    if (!p) return;
+    free_all(*p);
+    delete p;
+}
+
+const char *fstat_status_string(fstat_status s) {
+    switch (s) {
+        case FSTAT_OK: return "ok";
+        case FSTAT_ERR_ARG: return "invalid argument";
+        case FSTAT_ERR_OOM: return "out of memory";
+        case FSTAT_ERR_CUDA: return "CUDA error";
+        case FSTAT_ERR_OVERFLOW: return "candidate capacity exceeded";
+        case FSTAT_ERR_TIMEOUT: return "device wait timed out";
+        case FSTAT_ERR_STATE: return "plan poisoned by an earlier error";
+        case FSTAT_ERR_INTERNAL: return "internal error";
+    }
+    return "unknown status";
+}
+
+const char *fstat_plan_error(const fstat_plan *p) { return p ? p->err.c_str() : ""; }
+
+}  // extern "C"

@@ -1,0 +1,177 @@
+// Internal declarations shared by the host orchestration (api.cu) and the kernel
+// translation units.  Not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/fstat.h"
+
+namespace fstat {
+
+constexpr int kMinLogN = 8;    // n_fft >= 256
+constexpr int kMaxLogN = 20;   // n_fft <= 2^20
+
+// Split of a power-of-two transform length N = N1 * N2 into the two passes of
+// the four-step FFT: pass 1 transforms the N1 strided columns (length N2), pass
+// 2 the N2 rows (length N1).
+inline int log_n1(int logn) { return logn / 2; }
+inline int log_n2(int logn) { return logn - logn / 2; }
+
+// Twiddle tables of one transform length, forward direction e^{-2 pi i k / M}.
+struct TwiddleSet {
+    int logn = 0;
+    // device pointers, interleaved (re, im); float and double copies
+    const double *in1_d = nullptr, *in2_d = nullptr, *lo_d = nullptr, *hi_d = nullptr;
+    const float *in1_f = nullptr, *in2_f = nullptr, *lo_f = nullptr, *hi_f = nullptr;
+};
+
+// Device record of one candidate: global cell index, bin and F.
+struct CandRecord {
+    uint32_t cell;
+    uint32_t bin;
+    double F;
+};
+
+// Per-sky constants computed once per plan: unit vector and the coefficients of
+// a(h) = A0 cos2h + A1 sin2h + A2 cosh + A3 sinh + A4 and
+//       b(h) = B0 cos2h + B1 sin2h + B2 cosh + B3 sinh, h = alpha - LST.
+struct SkyConst {
+    double nx, ny, nz, alpha;
+    double A[5];
+    double B[4];
+};
+
+// Band data resident on the device.
+struct BandDev {
+    int64_t n = 0;
+    double dt = 0, f_off = 0, phi0 = 0, eps = 0;
+    int64_t n_fft = 0;
+    int logn = 0;
+    int64_t lo = 0, hi = 0;
+    double *x = nullptr;      // [n] float64 (converted from float32 when needed)
+    double *r = nullptr;      // [3n]
+    double *sigma2 = nullptr; // device scalar
+    void *xu = nullptr;       // [U n]: double (FP64 form) or float (FP32 form)
+};
+
+struct Plan {
+    fstat_plan_desc desc{};
+    std::vector<BandDev> bands;
+    std::vector<fstat_band> host_bands;
+    int64_t n_cells = 0, f_evals = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    bool poisoned = false;
+    std::string err;
+    int64_t launches = 0;
+    int64_t device_bytes = 0;
+    std::vector<void *> allocs;
+
+    // grids (device, and host copies for candidate retrieval)
+    double *alpha = nullptr, *delta = nullptr, *fdot = nullptr;
+    std::vector<double> h_alpha, h_delta, h_fdot;
+    int64_t n_fft_max = 0;
+    SkyConst *sky = nullptr;
+    uint64_t *chirp_fx = nullptr;  // per (band, spin): frac(fdot dt^2 / 2) in 2^-64 cycles
+    double *chirp_d = nullptr;     // per (band, spin): fdot dt^2 / 2 (FP64 form)
+
+    // per sky batch
+    int64_t sky_batch = 0;
+    void *w = nullptr;            // FP32: float4 [sky_batch][n_max]; FP64: double2 [2][n_max]
+    double *partials = nullptr;   // [sky_batch][n_blocks_max][3]
+    double *S = nullptr;          // [sky_batch][3]
+    double *norm = nullptr;       // [sky_batch][2]: 1/(sigma^2 S_aa), 1/(sigma^2 S_bb)
+    int64_t n_max = 0;
+
+    // FFT scratch (cell slots)
+    int64_t cell_batch = 0;
+    void *scratch = nullptr;
+
+    // Bluestein / generic-FFT work buffers (double2)
+    double *bw = nullptr;
+    int64_t bw_elems = 0;
+
+    // twiddles, one set per transform length used
+    std::vector<TwiddleSet> tw;
+    void *tw_pool = nullptr;
+
+    // candidates
+    CandRecord *cand = nullptr;
+    unsigned long long *cand_count = nullptr;
+    int64_t cand_capacity = 0;
+    int64_t last_total = 0;
+    bool searched = false;
+
+    // sampled per-kernel timing (fstat_plan_set_timing)
+    struct KStat {
+        std::string name;
+        int64_t launches = 0, timed = 0;
+        double ms = 0.0, flops = 0.0, bytes = 0.0;
+    };
+    struct Pending {
+        int stat;
+        cudaEvent_t a, b;
+    };
+    int timing_every = 0;
+    int64_t timing_tick = 0;
+    std::vector<KStat> kstats;
+    std::vector<Pending> pending;
+    std::vector<cudaEvent_t> ev_pool, ev_all;
+
+    const TwiddleSet *twiddles(int logn) const {
+        for (auto &t : tw)
+            if (t.logn == logn) return &t;
+        return nullptr;
+    }
+};
+
+// ---------------------------------------------------------------- launchers
+// Each returns the number of kernels it launched (for the plan's counter).
+
+// sigma^2 = (1/n) sum x^2, compensated, into *out (device); user_sigma2 > 0 overrides.
+// partials: >= 256 doubles.
+int launch_sigma2(const double *x, int64_t n, double user_sigma2, double *partials, double *out,
+                  cudaStream_t s);
+
+// Generic two-pass power-of-two FFT of `pairs` * 2 transforms of length 2^logn,
+// in[t] -> out[t] (t over 2*pairs contiguous transforms, interleaved complex).
+// dir = -1 forward, +1 inverse (unscaled).  FP64 or FP32 arithmetic.
+int launch_fft_generic(const TwiddleSet &tw, bool fp64, int dir, const void *in, void *out,
+                       int64_t n_transforms, void *scratch, cudaStream_t s);
+
+// Bluestein DFT of arbitrary length n (double2 in/out), using the generic FFT of
+// length M = 2^logm >= 2n - 1.  work holds 3*M double2.
+int launch_bluestein(const TwiddleSet &twm, int dir, const double *in, double *out, int64_t n,
+                     double *work, void *scratch, cudaStream_t s);
+
+// U-fold FFT upsample of x[n] (double) into xu[U n] (double or float).
+int launch_upsample(const Plan &p, const BandDev &b, int U, void *xu, bool xu_fp32,
+                    cudaStream_t s);
+
+// Per-sky constants for all sky positions of the plan.
+int launch_sky_consts(const double *alpha, const double *delta, int64_t n_sky, double lat,
+                      double gamma, SkyConst *out, cudaStream_t s);
+
+// Geometry + resampling + phase demodulation for skies [s0, s0+ns) of band b.
+// FP32 form writes w as float4 (y a, y b); FP64 form writes double2 wa, wb.
+// Optional diagnostics (nullptr to skip): y (double2), a, b (double), mask (uint8).
+int launch_geometry(const Plan &p, const BandDev &b, int64_t s0, int64_t ns, bool fp32,
+                    double *dbg_y, double *dbg_a, double *dbg_b, uint8_t *dbg_mask,
+                    cudaStream_t s);
+
+// Per-sky S sums and normalisations for the ns skies of the last geometry launch.
+int launch_reduce_norms(const Plan &p, const BandDev &b, int64_t ns, cudaStream_t s);
+
+// The two FFT passes of the search for cells [c0, c0 + nc) of band `band_idx`
+// (cells of this band: c = sky * n_spin + spin, skies relative to sky base s0).
+// `mid` (may be null) is recorded between the two passes.
+int launch_search_cells_f32(const Plan &p, int band_idx, const BandDev &b, int64_t s0,
+                            int64_t c0, int64_t nc, cudaStream_t s, cudaEvent_t mid);
+int launch_search_cells_f64(const Plan &p, int band_idx, const BandDev &b, int64_t s0,
+                            int64_t c0, int64_t nc, cudaStream_t s, cudaEvent_t mid);
+
+}  // namespace fstat

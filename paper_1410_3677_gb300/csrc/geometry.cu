@@ -1,0 +1,459 @@
+// Per-band and per-sky steps of the search (Sect. 2, Fig. 1):
+//   per band: noise variance, U-fold FFT upsample of the narrow-band series
+//             ("resampling ... using the FFT and splines");
+//   per sky:  Roemer delay nhat . r, detector time of every barycentric sample,
+//             amplitude modulations a(t), b(t), Keys-cubic resampling and the
+//             band-offset phase demodulation ("amplitude and phase
+//             demodulation", "resampling", done once per sky position), and the
+//             FP64 compensated sums S_aa, S_bb, S_ab.
+#include <math.h>
+
+#include "fstat_internal.h"
+
+namespace fstat {
+
+namespace {
+
+constexpr double kTwoPi = 6.283185307179586476925286766559;
+constexpr double kOmegaR = kTwoPi / 86164.0905;   // sidereal rotation rate, rad/s
+
+struct KahanD {
+    double s = 0.0, c = 0.0;
+    __device__ void add(double v) {
+        double y = v - c;
+        double t = s + y;
+        c = (t - s) - y;
+        s = t;
+    }
+};
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Sum of v over a 256-thread block into thread 0's return value.
+__device__ double block_sum256(double v, double *sh) {
+    v = warp_sum(v);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0) sh[w] = v;
+    __syncthreads();
+    double r = 0.0;
+    if (w == 0) {
+        r = (l < (int)(blockDim.x >> 5)) ? sh[l] : 0.0;
+        r = warp_sum(r);
+    }
+    __syncthreads();
+    return r;
+}
+
+// ------------------------------------------------------------------ sigma^2
+__global__ void __launch_bounds__(256) k_sumsq(const double *__restrict__ x, int64_t n,
+                                               double *__restrict__ partials) {
+    __shared__ double sh[8];
+    KahanD k;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        k.add(x[i] * x[i]);
+    const double s = block_sum256(k.s - k.c, sh);
+    if (threadIdx.x == 0) partials[blockIdx.x] = s;
+}
+
+__global__ void k_sigma2_final(const double *__restrict__ partials, int nblk, int64_t n,
+                               double user_sigma2, double *__restrict__ out) {
+    KahanD k;
+    for (int i = threadIdx.x; i < nblk; i += 32) k.add(partials[i]);
+    double s = warp_sum(k.s - k.c);
+    if (threadIdx.x == 0) *out = user_sigma2 > 0.0 ? user_sigma2 : s / (double)n;
+}
+
+// ------------------------------------------------------------------ sky constants
+// a(h), b(h) of a right-angle interferometer (Jaranowski, Krolak & Schutz 1998)
+// expanded in cos 2h, sin 2h, cos h, sin h with h = alpha - local sidereal time.
+__global__ void k_sky_consts(const double *__restrict__ alpha, const double *__restrict__ delta,
+                             int64_t n_sky, double lat, double gamma, SkyConst *__restrict__ out) {
+    const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (s >= n_sky) return;
+    const double al = alpha[s], de = delta[s];
+    double sd, cd, sa, ca;
+    sincos(de, &sd, &cd);
+    sincos(al, &sa, &ca);
+    const double s2g = sin(2.0 * gamma), c2g = cos(2.0 * gamma);
+    const double sl = sin(lat), cl = cos(lat), s2l = sin(2.0 * lat), c2l = cos(2.0 * lat);
+    const double s2d = 2.0 * sd * cd, c2d = cd * cd - sd * sd;
+    SkyConst c;
+    c.nx = cd * ca;
+    c.ny = cd * sa;
+    c.nz = sd;
+    c.alpha = al;
+    c.A[0] = (1.0 / 16.0) * s2g * (3.0 - c2l) * (3.0 - c2d);   // cos 2h
+    c.A[1] = -0.25 * c2g * sl * (3.0 - c2d);                   // sin 2h
+    c.A[2] = 0.25 * s2g * s2l * s2d;                           // cos h
+    c.A[3] = -0.5 * c2g * cl * s2d;                            // sin h
+    c.A[4] = 0.75 * s2g * cl * cl * cd * cd;                   // constant
+    c.B[0] = c2g * sl * sd;                                    // cos 2h
+    c.B[1] = 0.25 * s2g * (3.0 - c2l) * sd;                    // sin 2h
+    c.B[2] = c2g * cl * cd;                                    // cos h
+    c.B[3] = 0.5 * s2g * s2l * cd;                             // sin h
+    out[s] = c;
+}
+
+// ------------------------------------------------------------------ geometry
+struct GeoArgs {
+    const double *r;
+    const void *xu;
+    int64_t m_up;
+    int U;
+    int64_t n;
+    double dt, inv_dt, f_off, phi0;
+    const SkyConst *sky;
+    int64_t s0;
+    void *w;
+    int64_t w_stride;
+    double *partials;
+    int nblk;
+    double *dbg_y, *dbg_a, *dbg_b;
+    uint8_t *dbg_mask;
+};
+
+__device__ __forceinline__ double delay_at(const double *__restrict__ r, const SkyConst &sc,
+                                           int64_t j) {
+    return sc.nx * r[3 * j] + sc.ny * r[3 * j + 1] + sc.nz * r[3 * j + 2];
+}
+
+// Linear interpolation of the delay at fractional sample u; the end segments
+// extend beyond the data.
+__device__ __forceinline__ double delay_lin(const double *__restrict__ r, const SkyConst &sc,
+                                            int64_t n, double u) {
+    int64_t j = (int64_t)floor(u);
+    j = j < 0 ? 0 : (j > n - 2 ? n - 2 : j);
+    const double f = u - (double)j;
+    const double d0 = delay_at(r, sc, j), d1 = delay_at(r, sc, j + 1);
+    return d0 + f * (d1 - d0);
+}
+
+template <bool FP32>
+__global__ void __launch_bounds__(256) k_geometry(GeoArgs g) {
+    __shared__ double sh[8];
+    const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int sl = blockIdx.y;
+    const SkyConst sc = g.sky[g.s0 + sl];
+    double saa = 0.0, sbb = 0.0, sab = 0.0;
+    if (k < g.n) {
+        // detector time t of barycentric sample k: t = k dt - d(k dt - d(k dt))
+        const double dk = delay_at(g.r, sc, k);
+        const double u0 = (double)k - dk * g.inv_dt;
+        const double d1 = delay_lin(g.r, sc, g.n, u0);
+        const double u = (double)k - d1 * g.inv_dt;
+        const double d2 = delay_lin(g.r, sc, g.n, u);
+        const bool valid = (u >= 0.0) && (u <= (double)(g.n - 1));
+        const double t = u * g.dt;
+        const double h = sc.alpha - (g.phi0 + kOmegaR * t);
+        // Keys cubic (a = -1/2) on the upsampled series, periodic indexing
+        const double p = (double)g.U * u;
+        const double pf = floor(p);
+        int64_t i0 = (int64_t)pf - 1;
+        i0 %= g.m_up;
+        if (i0 < 0) i0 += g.m_up;
+        int64_t idx[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            int64_t v = i0 + q;
+            idx[q] = v >= g.m_up ? v - g.m_up : v;
+        }
+        // band-offset phase, cycles, reduced in FP64
+        const double cyc = g.f_off * d2;
+        const double fr = cyc - floor(cyc);
+        if constexpr (FP32) {
+            const float hr = (float)(h - kTwoPi * rint(h / kTwoPi));
+            float s1, c1;
+            sincosf(hr, &s1, &c1);
+            const float c2 = c1 * c1 - s1 * s1, s2 = 2.f * s1 * c1;
+            const float av = (float)sc.A[0] * c2 + (float)sc.A[1] * s2 + (float)sc.A[2] * c1 +
+                             (float)sc.A[3] * s1 + (float)sc.A[4];
+            const float bv = (float)sc.B[0] * c2 + (float)sc.B[1] * s2 + (float)sc.B[2] * c1 +
+                             (float)sc.B[3] * s1;
+            float yr = 0.f, yi = 0.f;
+            if (valid) {
+                const float mu = (float)(p - pf);
+                const float w0 = ((-0.5f * mu + 1.f) * mu - 0.5f) * mu;
+                const float w1 = (1.5f * mu - 2.5f) * mu * mu + 1.f;
+                const float w2 = ((-1.5f * mu + 2.f) * mu + 0.5f) * mu;
+                const float w3 = (0.5f * mu - 0.5f) * mu * mu;
+                const float *xu = (const float *)g.xu;
+                const float v = w0 * xu[idx[0]] + w1 * xu[idx[1]] + w2 * xu[idx[2]] + w3 * xu[idx[3]];
+                const float frs = (float)(fr - rint(fr));
+                float sp, cp;
+                sincospif(2.f * frs, &sp, &cp);
+                yr = v * cp;
+                yi = -v * sp;
+                saa = (double)av * av;
+                sbb = (double)bv * bv;
+                sab = (double)av * bv;
+            }
+            float4 *w = (float4 *)g.w + (int64_t)sl * g.w_stride;
+            w[k] = make_float4(yr * av, yi * av, yr * bv, yi * bv);
+            if (g.dbg_y) {
+                g.dbg_y[2 * k] = yr; g.dbg_y[2 * k + 1] = yi;
+                g.dbg_a[k] = av; g.dbg_b[k] = bv; g.dbg_mask[k] = valid;
+            }
+        } else {
+            double s1, c1;
+            sincos(h, &s1, &c1);
+            const double c2 = c1 * c1 - s1 * s1, s2 = 2.0 * s1 * c1;
+            const double av = sc.A[0] * c2 + sc.A[1] * s2 + sc.A[2] * c1 + sc.A[3] * s1 + sc.A[4];
+            const double bv = sc.B[0] * c2 + sc.B[1] * s2 + sc.B[2] * c1 + sc.B[3] * s1;
+            double yr = 0.0, yi = 0.0;
+            if (valid) {
+                const double mu = p - pf;
+                const double w0 = ((-0.5 * mu + 1.0) * mu - 0.5) * mu;
+                const double w1 = (1.5 * mu - 2.5) * mu * mu + 1.0;
+                const double w2 = ((-1.5 * mu + 2.0) * mu + 0.5) * mu;
+                const double w3 = (0.5 * mu - 0.5) * mu * mu;
+                const double *xu = (const double *)g.xu;
+                const double v = w0 * xu[idx[0]] + w1 * xu[idx[1]] + w2 * xu[idx[2]] + w3 * xu[idx[3]];
+                double sp, cp;
+                sincospi(2.0 * fr, &sp, &cp);
+                yr = v * cp;
+                yi = -v * sp;
+                saa = av * av;
+                sbb = bv * bv;
+                sab = av * bv;
+            }
+            // {y a, y b} as two double2 (32 bytes per sample)
+            double2 *w = (double2 *)g.w + 2 * ((int64_t)sl * g.w_stride + k);
+            w[0] = make_double2(yr * av, yi * av);
+            w[1] = make_double2(yr * bv, yi * bv);
+            if (g.dbg_y) {
+                g.dbg_y[2 * k] = yr; g.dbg_y[2 * k + 1] = yi;
+                g.dbg_a[k] = av; g.dbg_b[k] = bv; g.dbg_mask[k] = valid;
+            }
+        }
+    }
+    const double ta = block_sum256(saa, sh);
+    const double tb = block_sum256(sbb, sh);
+    const double tab = block_sum256(sab, sh);
+    if (threadIdx.x == 0) {
+        double *o = g.partials + ((int64_t)sl * g.nblk + blockIdx.x) * 3;
+        o[0] = ta; o[1] = tb; o[2] = tab;
+    }
+}
+
+// S sums per sky (Kahan over the block partials) and the normalisations
+// 1/(sigma^2 S_aa), 1/(sigma^2 S_bb).
+__global__ void k_reduce_norms(const double *__restrict__ partials, int nblk,
+                               const double *__restrict__ sigma2, double *__restrict__ S,
+                               double *__restrict__ norm) {
+    const int sl = blockIdx.x;
+    double out[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        KahanD k;
+        for (int i = threadIdx.x; i < nblk; i += 32) k.add(partials[((int64_t)sl * nblk + i) * 3 + c]);
+        out[c] = warp_sum(k.s - k.c);
+    }
+    if (threadIdx.x == 0) {
+        const double s2 = *sigma2;
+        S[3 * sl] = out[0];
+        S[3 * sl + 1] = out[1];
+        S[3 * sl + 2] = out[2];
+        norm[2 * sl] = out[0] > 0.0 ? 1.0 / (s2 * out[0]) : 0.0;
+        norm[2 * sl + 1] = out[1] > 0.0 ? 1.0 / (s2 * out[1]) : 0.0;
+    }
+}
+
+// ------------------------------------------------------------------ FFT upsample
+__global__ void k_real_to_cplx(const double *__restrict__ x, int64_t n, double2 *__restrict__ z) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) z[i] = make_double2(x[i], 0.0);
+}
+
+// Bluestein: c_m = e^{dir i pi (m^2 mod 2n)/n}; A = in * c (zero beyond n);
+// B = conj(c) wrapped around M so that the circular convolution is linear.
+__global__ void k_blue_prep(const double2 *__restrict__ in, int64_t n, int64_t M, int dir,
+                            double2 *__restrict__ A, double2 *__restrict__ B) {
+    const int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (m >= M) return;
+    double2 a = make_double2(0.0, 0.0), b = make_double2(0.0, 0.0);
+    int64_t mm = -1;
+    if (m < n) mm = m;
+    else if (m > M - n) mm = M - m;
+    if (mm >= 0) {
+        const int64_t q = (mm * mm) % (2 * n);
+        double s, c;
+        sincospi((double)dir * (double)q / (double)n, &s, &c);
+        b = make_double2(c, -s);
+        if (m < n) {
+            const double2 v = in[m];
+            a = make_double2(v.x * c - v.y * s, v.x * s + v.y * c);
+        }
+    }
+    A[m] = a;
+    B[m] = b;
+}
+
+__global__ void k_cmul_inplace(double2 *__restrict__ A, const double2 *__restrict__ B, int64_t M) {
+    const int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (m >= M) return;
+    const double2 a = A[m], b = B[m];
+    A[m] = make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+
+__global__ void k_blue_post(const double2 *__restrict__ A, int64_t n, int64_t M, int dir,
+                            double2 *__restrict__ out) {
+    const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const int64_t q = (k * k) % (2 * n);
+    double s, c;
+    sincospi((double)dir * (double)q / (double)n, &s, &c);
+    const double2 v = A[k];
+    const double inv = 1.0 / (double)M;
+    out[k] = make_double2((v.x * c - v.y * s) * inv, (v.x * s + v.y * c) * inv);
+}
+
+// Spectrum of the s-th sub-phase of the U-fold interpolant: Y_m = X_m e^{2 pi i m s/(U n)}
+// over signed frequencies; the Nyquist bin of an even n contributes X cos(pi s / U).
+__global__ void k_shift_spectrum(const double2 *__restrict__ X, int64_t n, int s, int U,
+                                 double2 *__restrict__ Y) {
+    const int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (m >= n) return;
+    const double2 v = X[m];
+    if ((n % 2 == 0) && m == n / 2) {
+        double c = cospi((double)s / (double)U);
+        Y[m] = make_double2(v.x * c, v.y * c);
+        return;
+    }
+    const int64_t ms = (2 * m < n) ? m : m - n;
+    const int64_t un = (int64_t)U * n;
+    int64_t q = (ms * s) % un;
+    if (q < 0) q += un;
+    double sn, cs;
+    sincospi(2.0 * (double)q / (double)un, &sn, &cs);
+    Y[m] = make_double2(v.x * cs - v.y * sn, v.x * sn + v.y * cs);
+}
+
+template <typename TO>
+__global__ void k_scatter_sub(const double2 *__restrict__ z, const double *__restrict__ x, int64_t n,
+                              int U, int s, TO *__restrict__ xu) {
+    const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    xu[(int64_t)U * k + s] = (TO)(s == 0 ? x[k] : z[k].x / (double)n);
+}
+
+inline unsigned blocks(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+}  // namespace
+
+// ================================================================== launchers
+int launch_sigma2(const double *x, int64_t n, double user_sigma2, double *partials,
+                  double *out, cudaStream_t s) {
+    constexpr int nblk = 256;
+    k_sumsq<<<nblk, 256, 0, s>>>(x, n, partials);
+    k_sigma2_final<<<1, 32, 0, s>>>(partials, nblk, n, user_sigma2, out);
+    return 2;
+}
+
+int launch_bluestein(const TwiddleSet &twm, int dir, const double *in, double *out, int64_t n,
+                     double *work, void *scratch, cudaStream_t s) {
+    const int64_t M = (int64_t)1 << twm.logn;
+    double2 *A = reinterpret_cast<double2 *>(work);
+    double2 *B = A + M;
+    int L = 0;
+    k_blue_prep<<<blocks(M, 256), 256, 0, s>>>(reinterpret_cast<const double2 *>(in), n, M, dir,
+                                                A, B);
+    ++L;
+    L += launch_fft_generic(twm, true, -1, A, A, 2, scratch, s);
+    k_cmul_inplace<<<blocks(M, 256), 256, 0, s>>>(A, B, M);
+    ++L;
+    L += launch_fft_generic(twm, true, +1, A, A, 1, scratch, s);
+    k_blue_post<<<blocks(n, 256), 256, 0, s>>>(A, n, M, dir, reinterpret_cast<double2 *>(out));
+    ++L;
+    return L;
+}
+
+static int dft_any(const Plan &p, int64_t n, int dir, double2 *z, double *work, cudaStream_t s) {
+    const bool pow2 = (n & (n - 1)) == 0 && n >= (1 << kMinLogN);
+    if (pow2) {
+        int lg = 0;
+        while ((int64_t(1) << lg) < n) ++lg;
+        return launch_fft_generic(*p.twiddles(lg), true, dir, z, z, 1, p.scratch, s);
+    }
+    int lm = kMinLogN;
+    while ((int64_t(1) << lm) < 2 * n - 1) ++lm;
+    return launch_bluestein(*p.twiddles(lm), dir, reinterpret_cast<double *>(z),
+                            reinterpret_cast<double *>(z), n, work, p.scratch, s);
+}
+
+int launch_upsample(const Plan &p, const BandDev &b, int U, void *xu, bool xu_fp32,
+                    cudaStream_t s) {
+    const int64_t n = b.n;
+    int L = 0;
+    if (U == 1) {
+        if (xu_fp32) k_scatter_sub<float><<<blocks(n, 256), 256, 0, s>>>(nullptr, b.x, n, 1, 0, (float *)xu);
+        else k_scatter_sub<double><<<blocks(n, 256), 256, 0, s>>>(nullptr, b.x, n, 1, 0, (double *)xu);
+        return 1;
+    }
+    double2 *X = reinterpret_cast<double2 *>(p.bw);
+    double2 *Y = X + p.n_max;
+    double *work = reinterpret_cast<double *>(Y + p.n_max);
+    k_real_to_cplx<<<blocks(n, 256), 256, 0, s>>>(b.x, n, X);
+    ++L;
+    L += dft_any(p, n, -1, X, work, s);
+    for (int sub = 0; sub < U; ++sub) {
+        if (sub > 0) {
+            k_shift_spectrum<<<blocks(n, 256), 256, 0, s>>>(X, n, sub, U, Y);
+            ++L;
+            L += dft_any(p, n, +1, Y, work, s);
+        }
+        if (xu_fp32)
+            k_scatter_sub<float><<<blocks(n, 256), 256, 0, s>>>(Y, b.x, n, U, sub, (float *)xu);
+        else
+            k_scatter_sub<double><<<blocks(n, 256), 256, 0, s>>>(Y, b.x, n, U, sub, (double *)xu);
+        ++L;
+    }
+    return L;
+}
+
+int launch_sky_consts(const double *alpha, const double *delta, int64_t n_sky, double lat,
+                      double gamma, SkyConst *out, cudaStream_t s) {
+    k_sky_consts<<<blocks(n_sky, 128), 128, 0, s>>>(alpha, delta, n_sky, lat, gamma, out);
+    return 1;
+}
+
+int launch_geometry(const Plan &p, const BandDev &b, int64_t s0, int64_t ns, bool fp32,
+                    double *dbg_y, double *dbg_a, double *dbg_b, uint8_t *dbg_mask,
+                    cudaStream_t s) {
+    GeoArgs g;
+    g.r = b.r;
+    g.xu = b.xu;
+    g.U = p.desc.upsample;
+    g.m_up = (int64_t)g.U * b.n;
+    g.n = b.n;
+    g.dt = b.dt;
+    g.inv_dt = 1.0 / b.dt;
+    g.f_off = b.f_off;
+    g.phi0 = b.phi0;
+    g.sky = p.sky;
+    g.s0 = s0;
+    g.w = p.w;
+    g.w_stride = p.n_max;
+    g.partials = p.partials;
+    g.nblk = (int)blocks(b.n, 256);
+    g.dbg_y = dbg_y;
+    g.dbg_a = dbg_a;
+    g.dbg_b = dbg_b;
+    g.dbg_mask = dbg_mask;
+    dim3 grid(g.nblk, (unsigned)ns);
+    if (fp32) k_geometry<true><<<grid, 256, 0, s>>>(g);
+    else k_geometry<false><<<grid, 256, 0, s>>>(g);
+    return 1;
+}
+
+int launch_reduce_norms(const Plan &p, const BandDev &b, int64_t ns, cudaStream_t s) {
+    k_reduce_norms<<<(unsigned)ns, 32, 0, s>>>(p.partials, (int)blocks(b.n, 256), b.sigma2, p.S,
+                                               p.norm);
+    return 1;
+}
+
+}  // namespace fstat

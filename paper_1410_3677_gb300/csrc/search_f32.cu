@@ -1,0 +1,9 @@
+// FP32 instantiations of the search passes (FSTAT_FP32_BATCHED).
+#include "search_launch.cuh"
+
+namespace fstat {
+int launch_search_cells_f32(const Plan &p, int band_idx, const BandDev &b, int64_t s0,
+                            int64_t c0, int64_t nc, cudaStream_t s, cudaEvent_t mid) {
+    return launch_search_dispatch<float>(p, band_idx, b, s0, c0, nc, s, mid);
+}
+}  // namespace fstat

@@ -1,0 +1,318 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle.
+
+F is compared bin by bin as |F_gpu - F_ref| / max(F_ref, 2) (2 = E[F] in
+noise): at most 1e-10 for the FP64 plain form and 1e-4 for the FP32 batched
+form.  Candidate lists must be identical except where |2F_ref - thr| is inside
+the tolerance band 2 tol max(F_ref, 2).
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1410_3677_gb300 import synth as S
+
+pytestmark = pytest.mark.gpu
+
+TOL = {0: 1e-10, 1: 1e-4}
+NTHREADS = os.cpu_count() or 4
+
+
+@pytest.fixture(scope="module")
+def fs():
+    from paper_1410_3677_gb300 import fstat
+    return fstat
+
+
+def _plan(fs, w, form, thr, bands=None, **kw):
+    args = dict(lat=w.lat, gamma=w.gamma, upsample=w.upsample, form=form,
+                cand_capacity=kw.pop("cand_capacity", 1 << 22))
+    args.update(kw)
+    return fs.Plan(bands if bands is not None else w.bands, w.alpha, w.delta, w.fdot, thr, **args)
+
+
+def _gpu_F(fs, w, form, cells_per_band=None, bins=None, **kw):
+    """F of every bin of every cell (threshold -1): {(band, sky, spin): F[bins]}."""
+    p = _plan(fs, w, form, -1.0, **kw)
+    rc = p.search()
+    assert rc == fs.FSTAT_OK
+    c, total = p.candidates()
+    assert total == c.size
+    info = p.info()
+    p.close()
+    return c, info
+
+
+def _oracle_F(w, band_idx, cells, bin_lo=0, bin_hi=0, sigma2=0.0, upsample=None):
+    b = w.bands[band_idx]
+    prm = O.params(w.lat, w.gamma, upsample or w.upsample, sigma2, False, 0)
+    cs = np.array([c[0] for c in cells])
+    cp = np.array([c[1] for c in cells])
+    return O.cells_F(b, prm, w.alpha, w.delta, w.fdot, cs, cp, bin_lo, bin_hi, NTHREADS)
+
+
+def _rel_err(F, ref):
+    return np.abs(F - ref) / np.maximum(ref, 2.0)
+
+
+def _check_all_bins(c, w, form, band_idx, cells, lo, hi, **okw):
+    ref = _oracle_F(w, band_idx, cells, lo if lo or hi else 0, hi if lo or hi else 0, **okw)
+    nb = ref.shape[1]
+    for i, (sk, sp) in enumerate(cells):
+        sel = c[(c["band"] == band_idx) & (c["sky"] == sk) & (c["spin"] == sp)]
+        assert sel.size == nb
+        assert np.array_equal(sel["bin"], np.arange(lo, lo + nb))
+        err = _rel_err(sel["F"], ref[i])
+        assert err.max() <= TOL[form], (sk, sp, err.max(), int(np.argmax(err)))
+    return ref
+
+
+# ------------------------------------------------------------------ per-sky stage
+@pytest.mark.parametrize("form", [0, 1])
+def test_sky_stage_matches_oracle(fs, form):
+    """Resampled, phase-demodulated series y, a(t), b(t), window mask and S sums
+    for several sky positions, including a band offset (Eq. 1)."""
+    w = S.workload(1)
+    band = S.make_band(8192, 2.0, 42, 1.3, w.alpha, w.delta, w.fdot, [],
+                       f_off=100 + (1 - 2 ** -5) * 12, n_fft=16384)
+    p = _plan(fs, w, form, 20.0, bands=[band])
+    prm = O.params(w.lat, w.gamma, 2, 0.0)
+    xu = O.upsample(band.x, 2)
+    tol = 1e-12 if form == 0 else 2e-6
+    for sky in (0, 7, 31):
+        g = p.debug_sky(0, sky, band.n)
+        r = O.sky_prepare(band, prm, xu, float(w.alpha[sky]), float(w.delta[sky]))
+        # the window edge is a comparison u <= n-1 in FP64 on both sides
+        assert np.array_equal(g["mask"], r["mask"])
+        assert np.max(np.abs(g["a"] - r["a"])) < tol
+        assert np.max(np.abs(g["b"] - r["b"])) < tol
+        assert np.max(np.abs(g["y"] - r["y"])) < tol * 10 * max(1.0, np.max(np.abs(r["y"])))
+        assert np.allclose(g["S"], r["S"], rtol=1e-12 if form == 0 else 1e-6)
+    p.close()
+
+
+# ------------------------------------------------------------------ all bins, tiny workload
+@pytest.mark.parametrize("form", [0, 1])
+def test_all_bins_tiny_workload(fs, form):
+    """Every bin of all 128 cells of the tiny workload (N=4096, N_fft=8192)."""
+    w = S.workload(1)
+    c, info = _gpu_F(fs, w, form)
+    assert info["f_evals"] == 128 * 4095
+    cells = [(s, j) for s in range(w.n_sky) for j in range(w.n_spin)]
+    _check_all_bins(c, w, form, 0, cells, 1, 4095)
+
+
+@pytest.mark.parametrize("form", [0, 1])
+def test_candidates_tiny_workload(fs, form):
+    """Threshold 2F > 20: same candidate list as the oracle outside the band."""
+    w = S.workload(1)
+    p = _plan(fs, w, form, w.thr_2F)
+    assert p.search() == fs.FSTAT_OK
+    c, total = p.candidates()
+    p.close()
+    prm = O.params(w.lat, w.gamma, w.upsample, 0.0, False, 0)
+    ref, rtot = O.search(w.bands, prm, w.alpha, w.delta, w.fdot, w.thr_2F, nthreads=NTHREADS)
+    _compare_candidates(c, ref, w, form)
+    inj = w.bands[0].injections[0]
+    hit = c[(c["sky"] == inj.sky) & (c["spin"] == inj.spin)]
+    assert hit["bin"][np.argmax(hit["F"])] == inj.bin
+    assert np.all(np.diff(c["sky"] * 10**12 + c["spin"] * 10**7 + c["bin"]) > 0)
+
+
+def _compare_candidates(c, ref, w, form, thr=None):
+    thr = w.thr_2F if thr is None else thr
+    tol = TOL[form]
+    key = lambda a: set(zip(a["band"].tolist(), a["sky"].tolist(), a["spin"].tolist(), a["bin"].tolist()))
+    kg, kr = key(c), key(ref)
+    refF = {k: f for k, f in zip(zip(ref["band"].tolist(), ref["sky"].tolist(), ref["spin"].tolist(),
+                                     ref["bin"].tolist()), ref["F"].tolist())}
+    gF = {k: f for k, f in zip(zip(c["band"].tolist(), c["sky"].tolist(), c["spin"].tolist(),
+                                   c["bin"].tolist()), c["F"].tolist())}
+    for k in kr - kg:     # missed by the GPU: must sit in the band
+        assert abs(2 * refF[k] - thr) <= 2 * tol * max(refF[k], 2.0) * 2, k
+    for k in kg - kr:     # extra on the GPU: its F must be within tolerance of the threshold
+        assert abs(2 * gF[k] - thr) <= 2 * tol * max(gF[k], 2.0) * 2, k
+    common = kg & kr
+    assert len(common) >= 0.99 * max(len(kr), 1)
+    for k in common:
+        assert abs(gF[k] - refF[k]) <= tol * max(refF[k], 2.0), k
+
+
+# ------------------------------------------------------------------ segment-length transforms
+@pytest.mark.parametrize("form", [0, 1])
+def test_all_bins_two_sidereal_days(fs, form):
+    """N = 86164 (two sidereal days at 2 s), N_fft = 2^18, injected signals: all
+    131071 bins of a few cells, including an injected cell."""
+    w = S.workload(2, n_sky=1024, n_spin=1)
+    inj = w.bands[0].injections[0]
+    skies = sorted({0, inj.sky, 700})
+    w2 = S.Workload(w.name, w.bands, w.alpha[skies], w.delta[skies], w.fdot, w.thr_2F)
+    c, _ = _gpu_F(fs, w2, form)
+    cells = [(i, 0) for i in range(len(skies))]
+    ref = _check_all_bins(c, w2, form, 0, cells, 1, (1 << 17) - 1)
+    k = skies.index(inj.sky)
+    assert np.argmax(ref[k]) + 1 == inj.bin
+
+
+@pytest.mark.parametrize("form", [0, 1])
+def test_uneven_bands_float32_band_offsets(fs, form):
+    """Three bands of 1, 2 and 4 sidereal days (N_fft 2^17, 2^18, 2^19), float32
+    samples, sigma != 1 and band offsets from Eq. 1, one plan."""
+    w0 = S.workload(4, n_sky=3, n_spin=2, n_bands=1)
+    bands = []
+    for i, days in enumerate((1, 2, 4)):
+        n = 43082 * days
+        bands.append(S.make_band(n, 2.0, 4000 + i, 0.5 + 0.6 * i, w0.alpha, w0.delta, w0.fdot, [],
+                                 f_off=100 + (1 - 2 ** -5) * (3 * i + 1), dtype=np.float32))
+    w = S.Workload("uneven", bands, w0.alpha, w0.delta, w0.fdot, 30.0)
+    c, info = _gpu_F(fs, w, form)
+    cells = [(s, j) for s in range(3) for j in range(2)]
+    for bi, b in enumerate(bands):
+        _check_all_bins(c, w, form, bi, cells, 1, b.n_fft // 2 - 1)
+
+
+# ------------------------------------------------------------------ edge cases
+@pytest.mark.parametrize("form", [0, 1])
+@pytest.mark.parametrize("n,n_fft,U", [(100, 256, 2), (129, 0, 1), (1000, 8192, 4), (4096, 8192, 3)])
+def test_small_and_odd_shapes(fs, form, n, n_fft, U):
+    """Smallest transform, odd length, explicit longer n_fft, U = 1, 3, 4."""
+    w0 = S.workload(1, n_sky=4, n_spin=2)
+    b = S.make_band(n, 2.0, 77 + n, 1.0, w0.alpha, w0.delta, w0.fdot, [], n_fft=n_fft)
+    w = S.Workload("small", [b], w0.alpha, w0.delta, w0.fdot, 10.0, upsample=U)
+    c, _ = _gpu_F(fs, w, form)
+    cells = [(s, j) for s in range(4) for j in range(2)]
+    _check_all_bins(c, w, form, 0, cells, 1, b.n_fft // 2 - 1, upsample=U)
+
+
+@pytest.mark.parametrize("form", [0, 1])
+def test_full_bin_range_and_given_sigma(fs, form):
+    """Bins [0, n_fft-1] (DC, Nyquist and negative frequencies) and a given sigma^2."""
+    w = S.workload(1, n_sky=3, n_spin=2)
+    c, _ = _gpu_F(fs, w, form, bin_lo=0, bin_hi=8191, sigma2=1.7)
+    cells = [(s, j) for s in range(3) for j in range(2)]
+    _check_all_bins(c, w, form, 0, cells, 0, 8191, sigma2=1.7)
+
+
+@pytest.mark.parametrize("form", [0, 1])
+def test_cell_ranges_resume(fs, form):
+    """Searching [a, b) then [b, n) gives the full search's candidates (resume at
+    any cell, including mid-sky), and an empty range gives none."""
+    w = S.workload(1)
+    p = _plan(fs, w, form, 12.0)
+    p.search()
+    full, _ = p.candidates()
+    parts = []
+    for a, b in ((0, 37), (37, 90), (90, 128)):
+        p.search(a, b)
+        c, _ = p.candidates()
+        cell = c["sky"] * w.n_spin + c["spin"]
+        assert np.all((cell >= a) & (cell < b))
+        parts.append(c)
+    assert np.array_equal(np.concatenate(parts), full)
+    p.search(5, 5)
+    c, total = p.candidates()
+    assert total == 0 and c.size == 0
+    p.close()
+
+
+@pytest.mark.parametrize("form", [0, 1])
+def test_overflow_keeps_exact_total(fs, form):
+    w = S.workload(1, n_sky=4, n_spin=4)
+    p = _plan(fs, w, form, -1.0, cand_capacity=1000)
+    assert p.search_status() == fs.FSTAT_ERR_OVERFLOW
+    rc, c, total = p.candidates_get_status(5000)
+    assert rc == fs.FSTAT_ERR_OVERFLOW
+    assert total == 16 * 4095 and c.size == 1000
+    rc, c, total = p.candidates_get_status(10)
+    assert rc == fs.FSTAT_ERR_OVERFLOW and c.size == 10
+    p.close()
+
+
+def test_allocation_failure_reports_oom_without_leak(fs):
+    import torch
+    w = S.workload(1)
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    for k in (1, 5, 12, 20):
+        os.environ["FSTAT_TEST_FAIL_ALLOC"] = str(k)
+        try:
+            with pytest.raises(fs.FstatError) as e:
+                _plan(fs, w, 1, 20.0)
+            assert e.value.code == fs.FSTAT_ERR_OOM
+        finally:
+            del os.environ["FSTAT_TEST_FAIL_ALLOC"]
+    torch.cuda.synchronize()
+    assert abs(torch.cuda.mem_get_info()[0] - free0) < (8 << 20)
+
+
+def test_fp32_matches_fp64_gpu(fs):
+    """The two GPU forms on the same grid agree within the FP32 tolerance."""
+    w = S.workload(1, n_sky=8, n_spin=4)
+    c0, _ = _gpu_F(fs, w, 0)
+    c1, _ = _gpu_F(fs, w, 1)
+    assert np.array_equal(c0["bin"], c1["bin"]) and np.array_equal(c0["sky"], c1["sky"])
+    assert np.max(_rel_err(c1["F"], c0["F"])) <= 1e-4
+
+
+def test_device_resident_inputs(fs):
+    """inputs_on_device = 1 (torch CUDA tensors) gives the host-input result."""
+    import torch
+    w = S.workload(1, n_sky=8, n_spin=4)
+    p = _plan(fs, w, 1, 20.0)
+    p.search()
+    ref, _ = p.candidates()
+    p.close()
+
+    class DB:
+        pass
+    dbs = []
+    for b in w.bands:
+        d = DB()
+        d.n, d.dt, d.f_off, d.phi0, d.eps, d.n_fft = b.n, b.dt, b.f_off, b.phi0, b.eps, b.n_fft
+        d.x = torch.from_numpy(b.x).cuda()
+        d.r = torch.from_numpy(np.ascontiguousarray(b.r)).cuda()
+        dbs.append(d)
+    p = fs.Plan(dbs, torch.from_numpy(w.alpha).cuda(), torch.from_numpy(w.delta).cuda(),
+                torch.from_numpy(w.fdot).cuda(), 20.0, lat=w.lat, gamma=w.gamma, form=1,
+                on_device=True)
+    p.search()
+    c, _ = p.candidates()
+    p.close()
+    assert np.array_equal(c, ref)
+
+
+# ------------------------------------------------------------------ full-size grid, sampled
+def test_precision_workload_full_grid_sampled(fs):
+    """The 4096 x 64 grid at N_fft = 2^18 in the FP32 batched launch configuration
+    the benchmark times, threshold 2F > 30; the candidates of sampled cells
+    (every injected cell and a few others) against the oracle, and the F of a
+    sample of all candidates recomputed one by one."""
+    w = S.workload(3)
+    p = _plan(fs, w, 1, w.thr_2F, cand_capacity=1 << 24)
+    assert p.search() == fs.FSTAT_OK
+    c, total = p.candidates()
+    p.close()
+    assert total == c.size
+    b = w.bands[0]
+    rng = np.random.default_rng(5)
+    cells = sorted({(i.sky, i.spin) for i in b.injections[:6]} |
+                   {(int(rng.integers(w.n_sky)), int(rng.integers(w.n_spin))) for _ in range(4)})
+    ref = _oracle_F(w, 0, cells)
+    for i, (sk, sp) in enumerate(cells):
+        sel = c[(c["sky"] == sk) & (c["spin"] == sp)]
+        want = np.nonzero(2 * ref[i] > w.thr_2F)[0] + 1
+        got = sel["bin"]
+        band = np.abs(2 * ref[i] - w.thr_2F) <= 2 * 2e-4 * np.maximum(ref[i], 2.0)
+        sym = set(want.tolist()) ^ set(got.tolist())
+        assert all(band[bn - 1] for bn in sym), (sk, sp, sym)
+        common = np.intersect1d(want, got)
+        if common.size:
+            Fg = sel["F"][np.isin(got, common)]
+            assert np.max(_rel_err(Fg, ref[i][common - 1])) <= 1e-4
+    # injections are found at their bin
+    for inj in b.injections:
+        sel = c[(c["sky"] == inj.sky) & (c["spin"] == inj.spin)]
+        if inj.snr >= 12:
+            assert sel.size and abs(int(sel["bin"][np.argmax(sel["F"])]) - inj.bin) <= 1

@@ -252,15 +252,19 @@ def _window_closed_forms(w, b, inj):
                                      (100.0 + (1 - 2 ** -5) * 7, 43082)])
 def test_noiseless_injection_closed_form(f_off, n):
     """Noiseless JKS signal exactly on (sky, fdot, bin): F equals the closed forms
-    (full: half the in-window SNR^2) within the resampling error (0.5%).  The
+    (full: half the in-window SNR^2) times the interpolation kernel's coherent gain
+    at the signal frequency, within 0.3%.  The
     band offset exercises the f_off phase demodulation (Eq. 1 band numbering);
     the one-sidereal-day case makes the delay vary enough to expose errors in it."""
     w, b, inj = _noiseless_injection(f_off, n)
     full, simp = _window_closed_forms(w, b, inj)
+    # the interpolation kernel passes a tone at nu cycles per upsampled sample
+    # with the position-averaged coherent gain |E_mu H(nu, mu)|^2
+    g = _keys_coherent_gain(inj.bin / (b.n_fft * 2))
     for full_form, ref in ((True, full), (False, simp)):
         prm = O.params(w.lat, w.gamma, 2, 1.0, full_form, 0)
         F = O.cells_F(b, prm, w.alpha, w.delta, w.fdot, [inj.sky], [inj.spin], inj.bin, inj.bin)
-        assert float(F[0, 0]) == pytest.approx(ref, rel=5e-3)
+        assert float(F[0, 0]) == pytest.approx(ref * g, rel=3e-3)
 
 
 def test_resampled_matches_brute_force_demodulated_dft():
@@ -308,6 +312,16 @@ def test_noise_identity_geometry_chi2_4():
         if full_form:
             assert stats.kstest(v, "chi2", args=(4,)).pvalue > 1e-3
             assert v.var() == pytest.approx(8.0, rel=0.03)
+
+
+def _keys_coherent_gain(nu):
+    """|E_mu sum_j w_j(mu) e^{2 pi i nu (j - mu)}|^2 for the Catmull-Rom weights
+    w_j (Keys 1981, a = -1/2) over taps j = -1..2 and uniform offsets mu."""
+    mu = (np.arange(4000) + 0.5) / 4000
+    w = np.stack([((-0.5 * mu + 1) * mu - 0.5) * mu, (1.5 * mu - 2.5) * mu * mu + 1,
+                  ((-1.5 * mu + 2) * mu + 0.5) * mu, (0.5 * mu - 0.5) * mu * mu])
+    h = np.sum(w * np.exp(2j * np.pi * nu * (np.arange(-1, 3)[:, None] - mu[None, :])), axis=0)
+    return float(np.abs(h.mean()) ** 2)
 
 
 def _keys_power_gain(nu):
