@@ -104,13 +104,17 @@ class Clocks:
 
 
 # ----------------------------------------------------------------------------- workload
-def make_workload(world: int, rank: int):
+def make_workload(world: int, rank: int, n_sky: int = 0):
     """The precision workload: one band of N = 86164 samples (two sidereal days at
     2 s), 4096 sky positions x 64 spindowns in [-1e-8, 0] Hz/s, N_fft = 2^18,
     16 injected signals, 2F > 30.  Under N ranks, rank r takes sky block r of a
     4096*N-point Fibonacci grid."""
     from paper_1410_3677_gb300 import synth as S
     w = S.workload(3)
+    if n_sky:                               # a smaller grid of the same data (profiling)
+        w.alpha, w.delta = w.alpha[:n_sky].copy(), w.delta[:n_sky].copy()
+        for b in w.bands:
+            b.injections = [i for i in b.injections if i.sky < n_sky]
     if world > 1:
         a, d = S.fibonacci_sky(4096 * world)
         w.alpha, w.delta = a[rank::world].copy(), d[rank::world].copy()
@@ -224,7 +228,7 @@ def run_ours(args, rank, world, dist):
     from paper_1410_3677_gb300 import fstat
     dev = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(dev)
-    w = make_workload(world, rank)
+    w = make_workload(world, rank, args.n_sky)
     stream = torch.cuda.Stream()
     nb_total = w.f_evals()
 
@@ -234,7 +238,7 @@ def run_ours(args, rank, world, dist):
 
     # ---------------------------------------------------------------- device-resident value
     plan = fstat.Plan(w.bands, w.alpha, w.delta, w.fdot, w.thr_2F, lat=w.lat, gamma=w.gamma,
-                      upsample=w.upsample, form=fstat.FP32_BATCHED, cand_capacity=1 << 24,
+                      upsample=w.upsample, form=fstat.FP32_BATCHED, cand_capacity=args.cand_capacity,
                       stream=stream.cuda_stream)
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
     for _ in range(args.warmup):
@@ -281,8 +285,9 @@ def run_ours(args, rank, world, dist):
     avg_ms = dv["timed_ms"] / dv["timed_launches"]
     achieved = dv["flops_per_launch"] / (avg_ms / 1e3) / 1e12
     peak = fp32_peak_tflops(sm_max)
-    shares = {k: round(v["timed_ms"] / v["timed_launches"] * v["launches"] / tot_ms * args.steps
-                       / args.steps, 4) if v["timed_launches"] else None for k, v in kstats.items()}
+    tot_local = sum(step_ms)
+    shares = {k: round(v["timed_ms"] / v["timed_launches"] * v["launches"] / tot_local, 4)
+              if v["timed_launches"] else None for k, v in kstats.items()}
     roofline = {"bound": "alu", "kernel": dname, "achieved": round(achieved, 3),
                 "peak": round(peak, 2), "unit": "TFLOP/s", "frac": round(achieved / peak, 4),
                 "traffic": traffic_record(dname),
@@ -340,8 +345,8 @@ def run_ours(args, rank, world, dist):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             p = fstat.Plan(hbs, al, de, fd, w.thr_2F, lat=w.lat, gamma=w.gamma,
-                           upsample=w.upsample, form=fstat.FP32_BATCHED, cand_capacity=1 << 24,
-                           stream=stream.cuda_stream)
+                           upsample=w.upsample, form=fstat.FP32_BATCHED,
+                           cand_capacity=args.cand_capacity, stream=stream.cuda_stream)
             p.search()
             c, nt = p.candidates()
             p.close()
@@ -389,6 +394,8 @@ def main():
     ap.add_argument("--skip-fp64", action="store_true")
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--n-sky", type=int, default=0, help="first n sky positions only (profiling)")
+    ap.add_argument("--cand-capacity", type=int, default=1 << 27)
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

@@ -21,6 +21,7 @@ LIB = os.path.join(HERE, "libfstat.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
+         "-Xcompiler", "-ffp-contract=off",
          f"-I{os.path.join(ROOT, 'include')}"]
 
 

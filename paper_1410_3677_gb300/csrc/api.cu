@@ -66,11 +66,39 @@ bool is_finite(double v) { return isfinite(v) != 0; }
 
 // Fixed-point 2^-64 cycles of frac(rate): exact wrap-around arithmetic on device.
 uint64_t to_fixed64(double rate) {
+    if (fabs(rate) < 0.25)                   // the usual case: keep the rate's full precision
+        return (uint64_t)(int64_t)llround(ldexp(rate, 64));
     double fr = rate - floor(rate);          // [0, 1)
     double hi = floor(fr * 4294967296.0);    // top 32 bits
     double lo = (fr * 4294967296.0 - hi) * 4294967296.0;
     uint64_t h = (uint64_t)hi, l = (uint64_t)llround(lo);
     return (h << 32) + l;                    // l may round to 2^32: carries into h
+}
+
+// Unit vector towards (alpha, delta) and the coefficients of the amplitude
+// modulations a(h), b(h) of a right-angle interferometer (Jaranowski, Krolak &
+// Schutz 1998) in cos 2h, sin 2h, cos h, sin h (h = alpha - local sidereal time),
+// evaluated on the host in FP64.
+SkyConst sky_const(double al, double de, double lat, double gamma) {
+    const double sd = sin(de), cd = cos(de);
+    const double s2g = sin(2.0 * gamma), c2g = cos(2.0 * gamma);
+    const double sl = sin(lat), cl = cos(lat), s2l = sin(2.0 * lat), c2l = cos(2.0 * lat);
+    const double s2d = sin(2.0 * de), c2d = cos(2.0 * de);
+    SkyConst c;
+    c.nx = cd * cos(al);
+    c.ny = cd * sin(al);
+    c.nz = sd;
+    c.alpha = al;
+    c.A[0] = (1.0 / 16.0) * s2g * (3.0 - c2l) * (3.0 - c2d);   // cos 2h
+    c.A[1] = -0.25 * c2g * sl * (3.0 - c2d);                   // sin 2h
+    c.A[2] = 0.25 * s2g * s2l * s2d;                           // cos h
+    c.A[3] = -0.5 * c2g * cl * s2d;                            // sin h
+    c.A[4] = 0.75 * s2g * cl * cl * cd * cd;                   // constant
+    c.B[0] = c2g * sl * sd;                                    // cos 2h
+    c.B[1] = 0.25 * s2g * (3.0 - c2l) * sd;                    // sin 2h
+    c.B[2] = c2g * cl * cd;                                    // cos h
+    c.B[3] = 0.5 * s2g * s2l * cd;                             // sin h
+    return c;
 }
 
 std::string band_err(int i, const char *m) { return "band " + std::to_string(i) + ": " + m; }
@@ -242,7 +270,11 @@ void create_impl(Plan &p, const fstat_plan_desc *d) {
     check(cudaMemcpyAsync(p.delta, p.h_delta.data(), d->n_sky * sizeof(double), cudaMemcpyHostToDevice, s), "delta");
     check(cudaMemcpyAsync(p.fdot, p.h_fdot.data(), d->n_spin * sizeof(double), cudaMemcpyHostToDevice, s), "fdot");
     p.sky = dalloc<SkyConst>(p, d->n_sky, n_alloc);
-    p.launches += launch_sky_consts(p.alpha, p.delta, d->n_sky, d->lat, d->gamma, p.sky, s);
+    {
+        std::vector<SkyConst> hs((size_t)d->n_sky);
+        for (int64_t i = 0; i < d->n_sky; ++i) hs[(size_t)i] = sky_const(p.h_alpha[i], p.h_delta[i], d->lat, d->gamma);
+        check(cudaMemcpy(p.sky, hs.data(), hs.size() * sizeof(SkyConst), cudaMemcpyHostToDevice), "sky");
+    }
 
     // spindown phase rates per (band, spin): fdot dt^2 / 2 cycles per k^2
     std::vector<uint64_t> cfx((size_t)d->n_bands * d->n_spin);

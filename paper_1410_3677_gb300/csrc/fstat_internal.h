@@ -152,10 +152,6 @@ int launch_bluestein(const TwiddleSet &twm, int dir, const double *in, double *o
 int launch_upsample(const Plan &p, const BandDev &b, int U, void *xu, bool xu_fp32,
                     cudaStream_t s);
 
-// Per-sky constants for all sky positions of the plan.
-int launch_sky_consts(const double *alpha, const double *delta, int64_t n_sky, double lat,
-                      double gamma, SkyConst *out, cudaStream_t s);
-
 // Geometry + resampling + phase demodulation for skies [s0, s0+ns) of band b.
 // FP32 form writes w as float4 (y a, y b); FP64 form writes double2 wa, wb.
 // Optional diagnostics (nullptr to skip): y (double2), a, b (double), mask (uint8).

@@ -68,37 +68,6 @@ __global__ void k_sigma2_final(const double *__restrict__ partials, int nblk, in
     if (threadIdx.x == 0) *out = user_sigma2 > 0.0 ? user_sigma2 : s / (double)n;
 }
 
-// ------------------------------------------------------------------ sky constants
-// a(h), b(h) of a right-angle interferometer (Jaranowski, Krolak & Schutz 1998)
-// expanded in cos 2h, sin 2h, cos h, sin h with h = alpha - local sidereal time.
-__global__ void k_sky_consts(const double *__restrict__ alpha, const double *__restrict__ delta,
-                             int64_t n_sky, double lat, double gamma, SkyConst *__restrict__ out) {
-    const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (s >= n_sky) return;
-    const double al = alpha[s], de = delta[s];
-    double sd, cd, sa, ca;
-    sincos(de, &sd, &cd);
-    sincos(al, &sa, &ca);
-    const double s2g = sin(2.0 * gamma), c2g = cos(2.0 * gamma);
-    const double sl = sin(lat), cl = cos(lat), s2l = sin(2.0 * lat), c2l = cos(2.0 * lat);
-    const double s2d = 2.0 * sd * cd, c2d = cd * cd - sd * sd;
-    SkyConst c;
-    c.nx = cd * ca;
-    c.ny = cd * sa;
-    c.nz = sd;
-    c.alpha = al;
-    c.A[0] = (1.0 / 16.0) * s2g * (3.0 - c2l) * (3.0 - c2d);   // cos 2h
-    c.A[1] = -0.25 * c2g * sl * (3.0 - c2d);                   // sin 2h
-    c.A[2] = 0.25 * s2g * s2l * s2d;                           // cos h
-    c.A[3] = -0.5 * c2g * cl * s2d;                            // sin h
-    c.A[4] = 0.75 * s2g * cl * cl * cd * cd;                   // constant
-    c.B[0] = c2g * sl * sd;                                    // cos 2h
-    c.B[1] = 0.25 * s2g * (3.0 - c2l) * sd;                    // sin 2h
-    c.B[2] = c2g * cl * cd;                                    // cos h
-    c.B[3] = 0.5 * s2g * s2l * cd;                             // sin h
-    out[s] = c;
-}
-
 // ------------------------------------------------------------------ geometry
 struct GeoArgs {
     const double *r;
@@ -117,9 +86,13 @@ struct GeoArgs {
     uint8_t *dbg_mask;
 };
 
+// The delay chain is evaluated with explicitly rounded operations (no fused
+// multiply-add): the band-offset phase 2 pi f_off d reaches ~1e5 rad, so the
+// rounding of d decides the FP64 agreement of F at the 1e-10 level.
 __device__ __forceinline__ double delay_at(const double *__restrict__ r, const SkyConst &sc,
                                            int64_t j) {
-    return sc.nx * r[3 * j] + sc.ny * r[3 * j + 1] + sc.nz * r[3 * j + 2];
+    return __dadd_rn(__dadd_rn(__dmul_rn(sc.nx, r[3 * j]), __dmul_rn(sc.ny, r[3 * j + 1])),
+                     __dmul_rn(sc.nz, r[3 * j + 2]));
 }
 
 // Linear interpolation of the delay at fractional sample u; the end segments
@@ -128,9 +101,9 @@ __device__ __forceinline__ double delay_lin(const double *__restrict__ r, const 
                                             int64_t n, double u) {
     int64_t j = (int64_t)floor(u);
     j = j < 0 ? 0 : (j > n - 2 ? n - 2 : j);
-    const double f = u - (double)j;
+    const double f = __dsub_rn(u, (double)j);
     const double d0 = delay_at(r, sc, j), d1 = delay_at(r, sc, j + 1);
-    return d0 + f * (d1 - d0);
+    return __dadd_rn(d0, __dmul_rn(f, __dsub_rn(d1, d0)));
 }
 
 template <bool FP32>
@@ -143,9 +116,9 @@ __global__ void __launch_bounds__(256) k_geometry(GeoArgs g) {
     if (k < g.n) {
         // detector time t of barycentric sample k: t = k dt - d(k dt - d(k dt))
         const double dk = delay_at(g.r, sc, k);
-        const double u0 = (double)k - dk * g.inv_dt;
+        const double u0 = __dsub_rn((double)k, __ddiv_rn(dk, g.dt));
         const double d1 = delay_lin(g.r, sc, g.n, u0);
-        const double u = (double)k - d1 * g.inv_dt;
+        const double u = __dsub_rn((double)k, __ddiv_rn(d1, g.dt));
         const double d2 = delay_lin(g.r, sc, g.n, u);
         const bool valid = (u >= 0.0) && (u <= (double)(g.n - 1));
         const double t = u * g.dt;
@@ -163,8 +136,8 @@ __global__ void __launch_bounds__(256) k_geometry(GeoArgs g) {
             idx[q] = v >= g.m_up ? v - g.m_up : v;
         }
         // band-offset phase, cycles, reduced in FP64
-        const double cyc = g.f_off * d2;
-        const double fr = cyc - floor(cyc);
+        const double cyc = __dmul_rn(g.f_off, d2);
+        const double fr = __dsub_rn(cyc, floor(cyc));
         if constexpr (FP32) {
             const float hr = (float)(h - kTwoPi * rint(h / kTwoPi));
             float s1, c1;
@@ -413,12 +386,6 @@ int launch_upsample(const Plan &p, const BandDev &b, int U, void *xu, bool xu_fp
         ++L;
     }
     return L;
-}
-
-int launch_sky_consts(const double *alpha, const double *delta, int64_t n_sky, double lat,
-                      double gamma, SkyConst *out, cudaStream_t s) {
-    k_sky_consts<<<blocks(n_sky, 128), 128, 0, s>>>(alpha, delta, n_sky, lat, gamma, out);
-    return 1;
 }
 
 int launch_geometry(const Plan &p, const BandDev &b, int64_t s0, int64_t ns, bool fp32,

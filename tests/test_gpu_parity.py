@@ -80,16 +80,21 @@ def test_sky_stage_matches_oracle(fs, form):
     p = _plan(fs, w, form, 20.0, bands=[band])
     prm = O.params(w.lat, w.gamma, 2, 0.0)
     xu = O.upsample(band.x, 2)
-    tol = 1e-12 if form == 0 else 2e-6
+    # a, b: closed forms; y: the band-offset phase 2 pi f_off d (~1e5 rad here)
+    # bounds the FP64 agreement near 1e-11 relative
+    tol_ab, tol_y, tol_S = (1e-12, 1e-10, 1e-12) if form == 0 else (2e-6, 2e-5, 1e-5)
     for sky in (0, 7, 31):
         g = p.debug_sky(0, sky, band.n)
         r = O.sky_prepare(band, prm, xu, float(w.alpha[sky]), float(w.delta[sky]))
         # the window edge is a comparison u <= n-1 in FP64 on both sides
-        assert np.array_equal(g["mask"], r["mask"])
-        assert np.max(np.abs(g["a"] - r["a"])) < tol
-        assert np.max(np.abs(g["b"] - r["b"])) < tol
-        assert np.max(np.abs(g["y"] - r["y"])) < tol * 10 * max(1.0, np.max(np.abs(r["y"])))
-        assert np.allclose(g["S"], r["S"], rtol=1e-12 if form == 0 else 1e-6)
+        bad = np.nonzero(g["mask"] != r["mask"])[0]
+        assert bad.size == 0, (sky, bad[:10], r["u"][bad[:10]])
+        ea, eb = np.max(np.abs(g["a"] - r["a"])), np.max(np.abs(g["b"] - r["b"]))
+        assert ea < tol_ab and eb < tol_ab, (sky, ea, eb)
+        ey = np.max(np.abs(g["y"] - r["y"])) / max(1.0, np.max(np.abs(r["y"])))
+        assert ey < tol_y, (sky, ey)
+        eS = np.max(np.abs(g["S"] - r["S"]) / np.abs(r["S"]))
+        assert eS < tol_S, (sky, g["S"], r["S"])
     p.close()
 
 
@@ -290,8 +295,8 @@ def test_precision_workload_full_grid_sampled(fs):
     (every injected cell and a few others) against the oracle, and the F of a
     sample of all candidates recomputed one by one."""
     w = S.workload(3)
-    p = _plan(fs, w, 1, w.thr_2F, cand_capacity=1 << 24)
-    assert p.search() == fs.FSTAT_OK
+    p = _plan(fs, w, 1, w.thr_2F, cand_capacity=1 << 27)
+    assert p.search() == fs.FSTAT_OK, p.error()
     c, total = p.candidates()
     p.close()
     assert total == c.size
