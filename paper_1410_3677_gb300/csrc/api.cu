@@ -37,6 +37,7 @@ void check(cudaError_t e, const char *what) {
 }
 
 struct OomError {};
+struct TimeoutError {};
 
 template <typename T>
 T *dalloc(Plan &p, size_t count, int &n_alloc) {
@@ -290,11 +291,18 @@ void create_impl(Plan &p, const fstat_plan_desc *d) {
     check(cudaMemcpy(p.chirp_fx, cfx.data(), cfx.size() * sizeof(uint64_t), cudaMemcpyHostToDevice), "chirp");
     check(cudaMemcpy(p.chirp_d, cd.data(), cd.size() * sizeof(double), cudaMemcpyHostToDevice), "chirp");
 
-    // per-sky-batch buffers
+    // per-sky-batch buffers; w rows padded to a multiple of each band's N1 so that
+    // column tiles of the first FFT pass never read past a sky's stretch
+    p.w_stride = p.n_max;
+    for (auto &b : p.bands) {
+        const int64_t n1 = int64_t(1) << log_n1(b.logn);
+        p.w_stride = std::max<int64_t>(p.w_stride, (b.n + n1 - 1) / n1 * n1);
+    }
     const int64_t nblk = (p.n_max + 255) / 256;
     p.sky_batch = fp32 ? std::min<int64_t>(d->n_sky, 64) : 1;
     const size_t w_elem = fp32 ? 16 : 32;
-    p.w = dalloc<unsigned char>(p, (size_t)p.sky_batch * p.n_max * w_elem, n_alloc);
+    p.w = dalloc<unsigned char>(p, (size_t)p.sky_batch * p.w_stride * w_elem, n_alloc);
+    check(cudaMemsetAsync(p.w, 0, (size_t)p.sky_batch * p.w_stride * w_elem, s), "memset");
     p.partials = dalloc<double>(p, std::max<int64_t>((int64_t)p.sky_batch * nblk * 3, 256), n_alloc);
     p.S = dalloc<double>(p, 3 * p.sky_batch, n_alloc);
     p.norm = dalloc<double>(p, 2 * p.sky_batch, n_alloc);
@@ -307,8 +315,19 @@ void create_impl(Plan &p, const fstat_plan_desc *d) {
     } else {
         p.cell_batch = 1;
     }
-    const size_t scratch_bytes = std::max<size_t>((size_t)p.cell_batch * 2 * max_nfft * tsz,
-                                                  (size_t)2 * std::max<int64_t>(max_m, p.n_max) * sizeof(double2) * 2);
+    size_t scratch_bytes = std::max<size_t>((size_t)p.cell_batch * 2 * max_nfft * tsz,
+                                            (size_t)2 * std::max<int64_t>(max_m, p.n_max) * sizeof(double2) * 2);
+    if (fp32) {
+        if (const char *v = getenv("FSTAT_PERSIST_BATCH")) p.pbatch = std::max(1, atoi(v));
+        if (const char *v = getenv("FSTAT_PERSIST_SLOTS")) p.pslots = std::max(2, atoi(v));
+        scratch_bytes = std::max<size_t>(scratch_bytes, (size_t)p.pslots * p.pbatch * 2 * max_nfft * sizeof(float2));
+        const int64_t nb_max = (p.sky_batch * d->n_spin + p.pbatch - 1) / p.pbatch + 1;
+        p.queue = dalloc<uint32_t>(p, (size_t)(1 + 2 * nb_max), n_alloc);
+        p.qerr = dalloc<uint32_t>(p, 1, n_alloc);
+        check(cudaMemsetAsync(p.qerr, 0, sizeof(uint32_t), s), "memset");
+        if (const char *v = getenv("FSTAT_TEST_WITHHOLD_ITEM")) p.withhold_item = atoll(v);
+        if (const char *v = getenv("FSTAT_BATCHED_LAUNCHES")) p.use_persistent = atoi(v) == 0;
+    }
     p.scratch = dalloc<unsigned char>(p, scratch_bytes, n_alloc);
     p.bw_elems = 2 * p.n_max + 2 * max_m;
     p.bw = dalloc<double>(p, 2 * (size_t)std::max<int64_t>(p.bw_elems, 1), n_alloc);
@@ -367,14 +386,19 @@ bool stat_launch(Plan &p, int idx, double flops, double bytes) {
 }
 
 void collect_timing(Plan &p) {
+    std::vector<cudaEvent_t> used;
     for (auto &pe : p.pending) {
         float ms = 0.f;
         check(cudaEventElapsedTime(&ms, pe.a, pe.b), "cudaEventElapsedTime");
         p.kstats[(size_t)pe.stat].timed += 1;
         p.kstats[(size_t)pe.stat].ms += ms;
-        p.ev_pool.push_back(pe.a);
-        p.ev_pool.push_back(pe.b);
+        used.push_back(pe.a);
+        used.push_back(pe.b);
     }
+    // an event may close one interval and open the next: return each once
+    std::sort(used.begin(), used.end());
+    used.erase(std::unique(used.begin(), used.end()), used.end());
+    for (cudaEvent_t e : used) p.ev_pool.push_back(e);
     p.pending.clear();
 }
 
@@ -395,6 +419,7 @@ void search_impl(Plan &p, int64_t begin, int64_t end) {
     const bool fp32 = d.form == FSTAT_FP32_BATCHED;
     cudaStream_t s = p.stream;
     check(cudaMemsetAsync(p.cand_count, 0, sizeof(unsigned long long), s), "memset");
+    if (p.qerr) check(cudaMemsetAsync(p.qerr, 0, sizeof(uint32_t), s), "memset");
     const int64_t per_band = d.n_sky * d.n_spin;
     for (int bi = 0; bi < d.n_bands; ++bi) {
         const int64_t b0 = (int64_t)bi * per_band;
@@ -409,6 +434,7 @@ void search_impl(Plan &p, int64_t begin, int64_t end) {
         const int i_geo = stat_index(p, "geometry_resample");
         const int i_p1 = stat_index(p, fp32 ? "fft_pass1_f32" : "fft_pass1_f64");
         const int i_p2 = stat_index(p, fp32 ? "fft_pass2_fstat_f32" : "fft_pass2_fstat_f64");
+        const int i_pp = stat_index(p, "fft_fstat_persistent_f32");
         const double welem = fp32 ? 16.0 : 32.0;
         for (int64_t sb = s_first; sb <= s_last; sb += p.sky_batch) {
             const int64_t ns = std::min<int64_t>(p.sky_batch, s_last + 1 - sb);
@@ -422,6 +448,15 @@ void search_impl(Plan &p, int64_t begin, int64_t end) {
             if (tg) { check(cudaEventRecord(g1, s), "event"); p.pending.push_back({i_geo, g0, g1}); }
             const int64_t c_lo = std::max<int64_t>(lc0, sb * d.n_spin);
             const int64_t c_hi = std::min<int64_t>(lc1, (sb + ns) * d.n_spin);
+            if (fp32 && p.use_persistent && persistent_supported(b.logn)) {
+                const bool tp = stat_launch(p, i_pp, 2.0 * (c_hi - c_lo) * 5.0 * nfft * (lg1 + lg2),
+                                            (double)ns * b.n * welem);
+                cudaEvent_t e0 = nullptr, e1 = nullptr;
+                if (tp) { e0 = ev_get(p); e1 = ev_get(p); check(cudaEventRecord(e0, s), "event"); }
+                p.launches += launch_search_persistent(p, bi, b, sb, c_lo, c_hi, s);
+                if (tp) { check(cudaEventRecord(e1, s), "event"); p.pending.push_back({i_pp, e0, e1}); }
+                continue;
+            }
             for (int64_t c = c_lo; c < c_hi; c += p.cell_batch) {
                 const int64_t nc = std::min<int64_t>(p.cell_batch, c_hi - c);
                 // 5 N log2 N per complex transform, split between the passes; two
@@ -450,6 +485,11 @@ void search_impl(Plan &p, int64_t begin, int64_t end) {
     check(cudaGetLastError(), "search launch");
     check(cudaStreamSynchronize(s), "search");
     collect_timing(p);
+    if (p.qerr) {
+        uint32_t e = 0;
+        check(cudaMemcpy(&e, p.qerr, sizeof(e), cudaMemcpyDeviceToHost), "queue status");
+        if (e) throw TimeoutError{};
+    }
     unsigned long long cnt = 0;
     check(cudaMemcpy(&cnt, p.cand_count, sizeof(cnt), cudaMemcpyDeviceToHost), "count");
     p.last_total = (int64_t)cnt;
@@ -470,6 +510,10 @@ fstat_status guarded(fstat_plan *p, F &&f) {
     } catch (const OomError &) {
         p->err = "out of device memory";
         return FSTAT_ERR_OOM;
+    } catch (const TimeoutError &) {
+        p->err = "a bounded device-side wait of the work queue ran out";
+        p->poisoned = true;
+        return FSTAT_ERR_TIMEOUT;
     } catch (const std::bad_alloc &) {
         p->err = "out of host memory";
         return FSTAT_ERR_OOM;

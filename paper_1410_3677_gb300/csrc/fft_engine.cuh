@@ -11,8 +11,11 @@
 // generated on the fly) and the last stage hands its outputs to a Storer
 // (global memory, or a fused epilogue), so the data crosses shared memory
 // (stages - 1) times.  Shared memory holds real and imaginary parts in separate
-// arrays with one pad word per 32, which keeps both the unit-stride and the
-// radix-strided accesses of a warp free of bank conflicts.
+// arrays; element i of sequence f lives at f*M + (i ^ (((i >> 3) ^ 17 f) & 31)),
+// an XOR swizzle inside each 32-word segment that keeps the unit-stride, the
+// radix-strided and the sequence-strided accesses of a warp (nearly) free of
+// bank conflicts without padding.  The twiddles of each stage sit in their own
+// table, ordered so that a warp reads consecutive words.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -27,14 +30,24 @@ __host__ __device__ constexpr int rem_radix(int M) { return M >> (3 * n_main(M))
 __host__ __device__ constexpr int n_stages(int M) { return n_main(M) + (rem_radix(M) > 1 ? 1 : 0); }
 __host__ __device__ constexpr int stage_radix(int M, int s) { return s < n_main(M) ? 8 : rem_radix(M); }
 __host__ __device__ constexpr int stage_ns(int M, int s) { return s < n_main(M) ? (1 << (3 * s)) : M / rem_radix(M); }
-__host__ __device__ constexpr int row_ld(int M) { return ((M + M / 32 + 1) % 2 == 0) ? (M + M / 32 + 2) : (M + M / 32 + 1); }
+// words of the per-stage twiddle tables: sum over stages s >= 1 of (R_s - 1) NS_s (< M)
+__host__ __device__ constexpr int tw_words(int M, int s = 1) {
+    return s >= n_stages(M) ? 0 : (stage_radix(M, s) - 1) * stage_ns(M, s) + tw_words(M, s + 1);
+}
+__host__ __device__ constexpr int tw_offset(int M, int s) {
+    return s <= 1 ? 0 : tw_offset(M, s - 1) + (stage_radix(M, s - 1) - 1) * stage_ns(M, s - 1);
+}
 
 template <typename T, int M, int F>
 constexpr size_t smem_bytes() {
-    return sizeof(T) * (size_t)(4 * F * row_ld(M) + 2 * M);
+    return sizeof(T) * (size_t)(4 * F * M + 2 * (tw_words(M) > 0 ? tw_words(M) : 1));
 }
 
-__device__ __forceinline__ int padi(int i) { return i + (i >> 5); }
+template <int M>
+__device__ __forceinline__ int sidx(int f, int i) {
+    constexpr int mask = M >= 32 ? 31 : M - 1;
+    return f * M + (i ^ (((i >> 3) ^ (17 * f)) & mask));
+}
 
 // ------------------------------------------------------------------ small DFTs
 // Natural order in and out; DIR = -1 computes sum_j v_j e^{-2 pi i jk/R}.
@@ -93,12 +106,28 @@ __device__ __forceinline__ void dft(T *re, T *im) {
     else if constexpr (R == 2) dft2<DIR>(re, im);
 }
 
+// ------------------------------------------------------------------ barriers
+// The whole CTA, or only the NT consumer threads of a warp-specialised CTA
+// (named barrier 1; thread indices 0 .. NT-1).
+struct CtaBarrier {
+    __device__ __forceinline__ static void sync() { __syncthreads(); }
+};
+template <int NT>
+struct NamedBarrier {
+    __device__ __forceinline__ static void sync() {
+        asm volatile("bar.sync 1, %0;" ::"n"(NT) : "memory");
+    }
+};
+
 // ------------------------------------------------------------------ the pass
 // MAPF: first and last stage map consecutive threads to consecutive sequences
 // (f fastest) -- used where the Loader/Storer walk a strided column tile, so that
 // a warp's global accesses cover contiguous columns.  Middle stages always map
 // consecutive threads to consecutive butterflies of one sequence.
-template <typename T, int M, int F, int EH, int DIR, bool MAPF, int S, class LD, class ST>
+// INPLACE: the Loader reads shared memory that the stage-0 scatter overwrites,
+// so the scatter waits for every thread's gather.
+template <typename T, int M, int F, int EH, int DIR, bool MAPF, int S, class LD, class ST,
+          class BAR = CtaBarrier, bool INPLACE = false>
 __device__ __forceinline__ void run_stage(T (&re)[2][EH], T (&im)[2][EH], T *sre, T *sim,
                                           const T *twr, const T *twi, LD &ld, ST &st) {
     constexpr int NST = n_stages(M);
@@ -107,41 +136,52 @@ __device__ __forceinline__ void run_stage(T (&re)[2][EH], T (&im)[2][EH], T *sre
     constexpr int NJ = EH / R;
     constexpr int JPF = M / R;
     constexpr int THREADS = F * M / EH;
-    constexpr int RLD = row_ld(M);
     constexpr bool ffast = MAPF && (S == 0 || S == NST - 1);
     static_assert(EH % R == 0, "elements per thread must be a multiple of the radix");
 
+    if constexpr (S == 0) {
+        // every global load of the tile is issued before any arithmetic
 #pragma unroll
-    for (int i = 0; i < NJ; ++i) {
-        const int q = threadIdx.x + i * THREADS;
-        const int f = ffast ? (q % F) : (q / JPF);
-        const int j = ffast ? (q / F) : (q % JPF);
-        T *ra = &re[0][i * R], *ia = &im[0][i * R], *rb = &re[1][i * R], *ib = &im[1][i * R];
-        if constexpr (S == 0) {
-            ld.template load<R, JPF>(f, j, ra, ia, rb, ib);
-        } else {
-            const T *pa_r = sre + f * RLD, *pa_i = sim + f * RLD;
-            const T *pb_r = sre + (F + f) * RLD, *pb_i = sim + (F + f) * RLD;
+        for (int i = 0; i < NJ; ++i) {
+            const int q = threadIdx.x + i * THREADS;
+            const int f = ffast ? (q % F) : (q / JPF);
+            const int j = ffast ? (q / F) : (q % JPF);
+            ld.template load<R, JPF>(f, j, &re[0][i * R], &im[0][i * R], &re[1][i * R],
+                                     &im[1][i * R]);
+        }
+#pragma unroll
+        for (int i = 0; i < NJ; ++i) {
+            dft<R, DIR>(&re[0][i * R], &im[0][i * R]);
+            dft<R, DIR>(&re[1][i * R], &im[1][i * R]);
+        }
+    } else {
+        const T *tr = twr + tw_offset(M, S), *ti = twi + tw_offset(M, S);
+#pragma unroll
+        for (int i = 0; i < NJ; ++i) {
+            const int q = threadIdx.x + i * THREADS;
+            const int f = ffast ? (q % F) : (q / JPF);
+            const int j = ffast ? (q / F) : (q % JPF);
+            T *ra = &re[0][i * R], *ia = &im[0][i * R], *rb = &re[1][i * R], *ib = &im[1][i * R];
 #pragma unroll
             for (int r = 0; r < R; ++r) {
-                const int idx = padi(j + r * JPF);
-                ra[r] = pa_r[idx]; ia[r] = pa_i[idx];
-                rb[r] = pb_r[idx]; ib[r] = pb_i[idx];
+                const int ia_ = sidx<M>(f, j + r * JPF), ib_ = sidx<M>(F + f, j + r * JPF);
+                ra[r] = sre[ia_]; ia[r] = sim[ia_];
+                rb[r] = sre[ib_]; ib[r] = sim[ib_];
             }
-            const int base = (j % NS) * (M / (NS * R));
+            // W_{NS R}^{r k}, k = j mod NS, from this stage's table [(r-1) NS + k]
+            const int k = j % NS;
 #pragma unroll
             for (int r = 1; r < R; ++r) {
-                const int e = r * base;
-                const T wr = twr[e];
-                const T wi = (DIR < 0) ? twi[e] : -twi[e];
+                const T wr = tr[(r - 1) * NS + k];
+                const T wi = (DIR < 0) ? ti[(r - 1) * NS + k] : -ti[(r - 1) * NS + k];
                 T xr = ra[r] * wr - ia[r] * wi, xi = ra[r] * wi + ia[r] * wr;
                 ra[r] = xr; ia[r] = xi;
                 xr = rb[r] * wr - ib[r] * wi; xi = rb[r] * wi + ib[r] * wr;
                 rb[r] = xr; ib[r] = xi;
             }
+            dft<R, DIR>(ra, ia);
+            dft<R, DIR>(rb, ib);
         }
-        dft<R, DIR>(ra, ia);
-        dft<R, DIR>(rb, ib);
     }
 
     if constexpr (S == NST - 1) {
@@ -154,44 +194,64 @@ __device__ __forceinline__ void run_stage(T (&re)[2][EH], T (&im)[2][EH], T *sre
                                       &im[1][i * R]);
         }
     } else {
-        if constexpr (S > 0) __syncthreads();   // every read of this stage is done
+        if constexpr (S > 0 || INPLACE) BAR::sync();   // every read of this stage is done
 #pragma unroll
         for (int i = 0; i < NJ; ++i) {
             const int q = threadIdx.x + i * THREADS;
             const int f = ffast ? (q % F) : (q / JPF);
             const int j = ffast ? (q / F) : (q % JPF);
             const int ob = (j / NS) * NS * R + (j % NS);
-            T *pa_r = sre + f * RLD, *pa_i = sim + f * RLD;
-            T *pb_r = sre + (F + f) * RLD, *pb_i = sim + (F + f) * RLD;
 #pragma unroll
             for (int r = 0; r < R; ++r) {
-                const int idx = padi(ob + r * NS);
-                pa_r[idx] = re[0][i * R + r]; pa_i[idx] = im[0][i * R + r];
-                pb_r[idx] = re[1][i * R + r]; pb_i[idx] = im[1][i * R + r];
+                const int ia_ = sidx<M>(f, ob + r * NS), ib_ = sidx<M>(F + f, ob + r * NS);
+                sre[ia_] = re[0][i * R + r]; sim[ia_] = im[0][i * R + r];
+                sre[ib_] = re[1][i * R + r]; sim[ib_] = im[1][i * R + r];
             }
         }
-        __syncthreads();
-        run_stage<T, M, F, EH, DIR, MAPF, S + 1>(re, im, sre, sim, twr, twi, ld, st);
+        BAR::sync();
+        run_stage<T, M, F, EH, DIR, MAPF, S + 1, LD, ST, BAR, INPLACE>(re, im, sre, sim, twr, twi,
+                                                                         ld, st);
     }
+}
+
+// Fills the per-stage twiddle tables from the forward table e^{-2 pi i k/M}:
+// stage s, entry (r-1) NS + k holds W_{NS R}^{r k} = W_M^{r k M/(NS R)}.
+template <typename T, int M, int THREADS, int S>
+__device__ __forceinline__ void fill_twiddles(T *twr, T *twi, const T *__restrict__ tw) {
+    if constexpr (S < n_stages(M)) {
+        constexpr int R = stage_radix(M, S), NS = stage_ns(M, S);
+        constexpr int n = (R - 1) * NS, off = tw_offset(M, S), step = M / (NS * R);
+        for (int e = (int)threadIdx.x; e < n; e += THREADS) {
+            const int r = e / NS + 1, k = e % NS;
+            const int m = r * k * step;
+            twr[off + e] = tw[2 * m];
+            twi[off + e] = tw[2 * m + 1];
+        }
+        fill_twiddles<T, M, THREADS, S + 1>(twr, twi, tw);
+    }
+}
+
+// One tile whose input the Loader reads from shared memory that is then reused
+// in place for the stage exchanges (persistent kernels); twiddle tables filled.
+template <typename T, int M, int F, int EH, int DIR, bool MAPF, class BAR, class LD, class ST>
+__device__ __forceinline__ void run_tile_inplace(LD &ld, ST &st, T *buf, const T *twr,
+                                                 const T *twi) {
+    T re[2][EH], im[2][EH];
+    run_stage<T, M, F, EH, DIR, MAPF, 0, LD, ST, BAR, true>(re, im, buf, buf + 2 * F * M, twr, twi,
+                                                            ld, st);
 }
 
 // One pass over a tile.  tw: forward twiddles e^{-2 pi i k/M}, k < M, interleaved.
 template <typename T, int M, int F, int EH, int DIR, bool MAPF, class LD, class ST>
 __device__ __forceinline__ void run_pass(LD &ld, ST &st, const T *__restrict__ tw) {
     constexpr int THREADS = F * M / EH;
-    constexpr int RLD = row_ld(M);
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *sre = reinterpret_cast<T *>(smem_raw);
-    T *sim = sre + 2 * F * RLD;
-    T *twr = sim + 2 * F * RLD;
-    T *twi = twr + M;
-    if constexpr (n_stages(M) > 1) {
-        for (int i = threadIdx.x; i < M; i += THREADS) {
-            twr[i] = tw[2 * i];
-            twi[i] = tw[2 * i + 1];
-        }
-        // made visible by the barrier that precedes the first shared-memory read
-    }
+    T *sim = sre + 2 * F * M;
+    T *twr = sim + 2 * F * M;
+    T *twi = twr + (tw_words(M) > 0 ? tw_words(M) : 1);
+    // made visible by the barrier that precedes the first shared-memory read
+    fill_twiddles<T, M, THREADS, 1>(twr, twi, tw);
     T re[2][EH], im[2][EH];
     run_stage<T, M, F, EH, DIR, MAPF, 0>(re, im, sre, sim, twr, twi, ld, st);
 }

@@ -90,6 +90,14 @@ struct Plan {
     // FFT scratch (cell slots)
     int64_t cell_batch = 0;
     void *scratch = nullptr;
+    int64_t w_stride = 0;          // per-sky stride of w, >= every band's n rounded up to N1
+
+    // persistent FP32 search: cells per batch, scratch ring slots, queue counters
+    int64_t pbatch = 2, pslots = 8;
+    uint32_t *queue = nullptr;     // [head | done1[nb] | done2[nb]]
+    uint32_t *qerr = nullptr;      // error word (bit 0: a bounded wait ran out)
+    int64_t withhold_item = -1;    // test hook (FSTAT_TEST_WITHHOLD_ITEM)
+    bool use_persistent = true;    // FSTAT_BATCHED_LAUNCHES=1: two launches per cell batch
 
     // Bluestein / generic-FFT work buffers (double2)
     double *bw = nullptr;
@@ -164,6 +172,13 @@ int launch_reduce_norms(const Plan &p, const BandDev &b, int64_t ns, cudaStream_
 
 // The two FFT passes of the search for cells [c0, c0 + nc) of band `band_idx`
 // (cells of this band: c = sky * n_spin + spin, skies relative to sky base s0).
+// Persistent FP32 search of band-local cells [c_lo, c_hi) of one sky batch
+// (skies from s0): both passes in one launch fed by a device work queue.
+bool persistent_supported(int logn);
+int persistent_tiles_per_cell(int logn);
+int launch_search_persistent(const Plan &p, int band_idx, const BandDev &b, int64_t s0,
+                             int64_t c_lo, int64_t c_hi, cudaStream_t s);
+
 // `mid` (may be null) is recorded between the two passes.
 int launch_search_cells_f32(const Plan &p, int band_idx, const BandDev &b, int64_t s0,
                             int64_t c0, int64_t nc, cudaStream_t s, cudaEvent_t mid);

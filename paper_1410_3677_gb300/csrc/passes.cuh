@@ -40,6 +40,8 @@ struct Cfg {
     static constexpr int THREADS = F * M / EH;
     static constexpr int TILES = OTHER / F;
     static constexpr size_t SMEM = eng::smem_bytes<T, M, F>();
+    // two resident CTAs per SM: at most 128 registers per thread at 256 threads
+    static constexpr int MIN_BLOCKS = THREADS >= 128 ? 2 : 1;
     static_assert(THREADS >= 1 && THREADS <= 256, "tile shape");
 };
 
@@ -104,21 +106,22 @@ struct SearchLoadF32 {
     template <int R, int JPF>
     __device__ __forceinline__ void load(int f, int j, float *ra, float *ia, float *rb,
                                          float *ib) const {
+        float4 v[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {      // loads first: all in flight together
+            const int k = k1_0 + f + C::N1 * (j + r * JPF);
+            v[r] = k < n ? __ldg(ws + k) : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
 #pragma unroll
         for (int r = 0; r < R; ++r) {
-            const int k = k1_0 + f + C::N1 * (j + r * JPF);
-            if (k < n) {
-                const float4 v = ws[k];
-                const uint64_t kk = (uint64_t)k * (uint64_t)k;
-                const int32_t top = (int32_t)((afx * kk) >> 32);          // cycles in [-1/2, 1/2)
-                const float ph = (float)top * 1.4629180792671596e-09f;    // 2 pi / 2^32
-                float s, c;
-                __sincosf(ph, &s, &c);
-                ra[r] = v.x * c + v.y * s; ia[r] = v.y * c - v.x * s;
-                rb[r] = v.z * c + v.w * s; ib[r] = v.w * c - v.z * s;
-            } else {
-                ra[r] = 0.f; ia[r] = 0.f; rb[r] = 0.f; ib[r] = 0.f;
-            }
+            const uint32_t k = (uint32_t)(k1_0 + f + C::N1 * (j + r * JPF));
+            const uint64_t kk = (uint64_t)k * (uint64_t)k;
+            const int32_t top = (int32_t)((afx * kk) >> 32);          // cycles in [-1/2, 1/2)
+            const float ph = (float)top * 1.4629180792671596e-09f;    // 2 pi / 2^32
+            float s, c;
+            __sincosf(ph, &s, &c);
+            ra[r] = v[r].x * c + v[r].y * s; ia[r] = v[r].y * c - v[r].x * s;
+            rb[r] = v[r].z * c + v[r].w * s; ib[r] = v[r].w * c - v[r].z * s;
         }
     }
 };
@@ -188,14 +191,19 @@ struct ScratchStore {
     }
     template <int R, int JPF>
     __device__ __forceinline__ void store(int f, int j, T *ra, T *ia, T *rb, T *ib) const {
+        using V = typename Vec2<T>::type;
         const int k1 = k1_0 + f;
+        V th[R], tl[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {      // table loads first
+            const int m = k1 * (j + r * JPF);
+            th[r] = __ldg(reinterpret_cast<const V *>(hi) + (m >> C::LOGN1));
+            tl[r] = __ldg(reinterpret_cast<const V *>(lo) + (m & (C::N1 - 1)));
+        }
 #pragma unroll
         for (int r = 0; r < R; ++r) {
             const int l2 = j + r * JPF;
-            const int m = k1 * l2;
-            const int mh = m >> C::LOGN1, ml = m & (C::N1 - 1);
-            const T hr = hi[2 * mh], hi_ = hi[2 * mh + 1], lr = lo[2 * ml], li = lo[2 * ml + 1];
-            T wr = hr * lr - hi_ * li, wi = hr * li + hi_ * lr;
+            T wr = th[r].x * tl[r].x - th[r].y * tl[r].y, wi = th[r].x * tl[r].y + th[r].y * tl[r].x;
             if (DIR > 0) wi = -wi;
             T xr = ra[r], xi = ia[r];
             cmul_tw(xr, xi, wr, wi);
@@ -323,7 +331,7 @@ struct SearchEpi {
 
 // ------------------------------------------------------------------ kernels
 template <typename T, int LOGN, int PASS, int DIR, bool MAPF, class LD, class ST>
-__global__ void __launch_bounds__(Cfg<T, LOGN, PASS>::THREADS)
+__global__ void __launch_bounds__(Cfg<T, LOGN, PASS>::THREADS, Cfg<T, LOGN, PASS>::MIN_BLOCKS)
 k_pass(LD ld, ST st, const T *__restrict__ tw) {
     using C = Cfg<T, LOGN, PASS>;
     ld.init();

@@ -1,0 +1,83 @@
+"""The persistent FP32 search kernel and its device work queue.
+
+Its per-element arithmetic is the same as the two-launches-per-batch form, so the
+candidates must agree bit for bit, whatever the batch size and the number of
+scratch slots.  A withheld completion (test hook) must end the search with
+FSTAT_ERR_TIMEOUT after the bounded waits run out, leaving the GPU usable.
+"""
+import os
+import time
+
+import numpy as np
+import pytest
+
+from paper_1410_3677_gb300 import synth as S
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def fs():
+    from paper_1410_3677_gb300 import fstat
+    return fstat
+
+
+def _run(fs, w, thr, env=None, **kw):
+    old = {}
+    for k, v in (env or {}).items():
+        old[k] = os.environ.get(k)
+        os.environ[k] = v
+    try:
+        p = fs.Plan(w.bands, w.alpha, w.delta, w.fdot, thr, lat=w.lat, gamma=w.gamma,
+                    upsample=w.upsample, form=fs.FP32_BATCHED, cand_capacity=1 << 22, **kw)
+    finally:
+        for k, v in old.items():
+            if v is None:
+                del os.environ[k]
+            else:
+                os.environ[k] = v
+    rc = p.search_status()
+    c, total = p.candidates() if rc in (fs.FSTAT_OK, fs.FSTAT_ERR_OVERFLOW) else (None, None)
+    return p, rc, c, total
+
+
+@pytest.mark.parametrize("env", [{"FSTAT_PERSIST_BATCH": "1", "FSTAT_PERSIST_SLOTS": "2"},
+                                 {"FSTAT_PERSIST_BATCH": "3", "FSTAT_PERSIST_SLOTS": "3"},
+                                 {"FSTAT_PERSIST_BATCH": "5", "FSTAT_PERSIST_SLOTS": "8"}])
+def test_queue_matches_batched_launches_bitwise(fs, env):
+    """Tiny workload (N_fft = 2^13) and a two-sidereal-day band (2^18) with cell
+    counts that leave a partial last batch."""
+    for w in (S.workload(1, n_sky=9, n_spin=3), S.workload(3, n_sky=5, n_spin=3)):
+        p0, rc0, ref, t0 = _run(fs, w, 8.0, {"FSTAT_BATCHED_LAUNCHES": "1"})
+        p0.close()
+        p1, rc1, got, t1 = _run(fs, w, 8.0, env)
+        p1.close()
+        assert rc0 == rc1 == fs.FSTAT_OK
+        assert t0 == t1 and np.array_equal(ref, got)
+
+
+def test_queue_cell_ranges(fs):
+    """Ranges that start and end inside a sky position and a batch."""
+    w = S.workload(1, n_sky=7, n_spin=5)
+    p, rc, full, _ = _run(fs, w, 6.0, {"FSTAT_PERSIST_BATCH": "4"})
+    parts = []
+    for a, b in ((0, 3), (3, 17), (17, 35)):
+        p.search(a, b)
+        parts.append(p.candidates()[0])
+    p.close()
+    assert np.array_equal(np.concatenate(parts), full)
+
+
+def test_withheld_completion_times_out_and_gpu_stays_usable(fs):
+    w = S.workload(1, n_sky=8, n_spin=4)
+    t0 = time.time()
+    p, rc, _, _ = _run(fs, w, 20.0, {"FSTAT_TEST_WITHHOLD_ITEM": "0"})
+    elapsed = time.time() - t0
+    assert rc == fs.FSTAT_ERR_TIMEOUT
+    assert elapsed < 30.0
+    assert "wait" in p.error()
+    assert p.search_status() == fs.FSTAT_ERR_STATE      # poisoned
+    p.close()
+    p, rc, c, total = _run(fs, w, 20.0)                 # a fresh plan works
+    p.close()
+    assert rc == fs.FSTAT_OK and total > 0
