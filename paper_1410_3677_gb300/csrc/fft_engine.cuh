@@ -10,12 +10,13 @@
 // memory.  The first stage reads through a Loader (global memory, or values
 // generated on the fly) and the last stage hands its outputs to a Storer
 // (global memory, or a fused epilogue), so the data crosses shared memory
-// (stages - 1) times.  Shared memory holds real and imaginary parts in separate
-// arrays; element i of sequence f lives at f*M + (i ^ (((i >> 3) ^ 17 f) & 31)),
-// an XOR swizzle inside each 32-word segment that keeps the unit-stride, the
-// radix-strided and the sequence-strided accesses of a warp (nearly) free of
-// bank conflicts without padding.  The twiddles of each stage sit in their own
-// table, ordered so that a warp reads consecutive words.
+// (stages - 1) times.  Shared memory holds complex elements (float2/double2)
+// in rows of LD elements; element i of a row sits at pad(i) = i + i/16 + i/128,
+// which spreads the radix-strided accesses of a warp over the banks and makes
+// pad(j + r s) = pad(j) + pad(r s) for every stride s the stages use, so each
+// thread forms one row address per job and reaches the R elements with
+// immediate offsets.  The twiddles of each stage sit in their own table, in the
+// order a warp reads them.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -23,6 +24,10 @@
 
 namespace fstat {
 namespace eng {
+
+template <typename T> struct Vec2T;
+template <> struct Vec2T<float> { using type = float2; };
+template <> struct Vec2T<double> { using type = double2; };
 
 __host__ __device__ constexpr int ilog2c(int x) { return x <= 1 ? 0 : 1 + ilog2c(x >> 1); }
 __host__ __device__ constexpr int n_main(int M) { return ilog2c(M) / 3; }
@@ -38,16 +43,18 @@ __host__ __device__ constexpr int tw_offset(int M, int s) {
     return s <= 1 ? 0 : tw_offset(M, s - 1) + (stage_radix(M, s - 1) - 1) * stage_ns(M, s - 1);
 }
 
-template <typename T, int M, int F>
-constexpr size_t smem_bytes() {
-    return sizeof(T) * (size_t)(4 * F * M + 2 * (tw_words(M) > 0 ? tw_words(M) : 1));
-}
+__host__ __device__ constexpr int pad(int i) { return i + (i >> 4) + (i >> 7); }
+// row length in elements: odd, so that rows of different sequences start in
+// different banks
+__host__ __device__ constexpr int row_ld(int M) { return (pad(M - 1) + 1) | 1; }
+__host__ __device__ constexpr int tw_entries(int M) { return tw_words(M) > 0 ? tw_words(M) : 1; }
 
-template <int M>
-__device__ __forceinline__ int sidx(int f, int i) {
-    constexpr int mask = M >= 32 ? 31 : M - 1;
-    return f * M + (i ^ (((i >> 3) ^ (17 * f)) & mask));
-}
+// bytes of the exchange area of a tile (2 transforms x F rows) and of a whole
+// non-persistent pass (exchange + twiddle table)
+template <typename T, int M, int F>
+__host__ __device__ constexpr size_t exch_bytes() { return 2 * sizeof(T) * (size_t)(2 * F * row_ld(M)); }
+template <typename T, int M, int F>
+__host__ __device__ constexpr size_t smem_bytes() { return exch_bytes<T, M, F>() + 2 * sizeof(T) * (size_t)tw_entries(M); }
 
 // ------------------------------------------------------------------ small DFTs
 // Natural order in and out; DIR = -1 computes sum_j v_j e^{-2 pi i jk/R}.
@@ -128,19 +135,22 @@ struct NamedBarrier {
 // so the scatter waits for every thread's gather.
 template <typename T, int M, int F, int EH, int DIR, bool MAPF, int S, class LD, class ST,
           class BAR = CtaBarrier, bool INPLACE = false>
-__device__ __forceinline__ void run_stage(T (&re)[2][EH], T (&im)[2][EH], T *sre, T *sim,
-                                          const T *twr, const T *twi, LD &ld, ST &st) {
+__device__ __forceinline__ void run_stage(T (&re)[2][EH], T (&im)[2][EH],
+                                          typename Vec2T<T>::type *sd,
+                                          const typename Vec2T<T>::type *tw, LD &ld, ST &st) {
+    using V = typename Vec2T<T>::type;
     constexpr int NST = n_stages(M);
     constexpr int R = stage_radix(M, S);
     constexpr int NS = stage_ns(M, S);
     constexpr int NJ = EH / R;
     constexpr int JPF = M / R;
     constexpr int THREADS = F * M / EH;
+    constexpr int RL = row_ld(M);
     constexpr bool ffast = MAPF && (S == 0 || S == NST - 1);
     static_assert(EH % R == 0, "elements per thread must be a multiple of the radix");
 
     if constexpr (S == 0) {
-        // every global load of the tile is issued before any arithmetic
+        // every load of the tile is issued before any arithmetic
 #pragma unroll
         for (int i = 0; i < NJ; ++i) {
             const int q = threadIdx.x + i * THREADS;
@@ -155,25 +165,27 @@ __device__ __forceinline__ void run_stage(T (&re)[2][EH], T (&im)[2][EH], T *sre
             dft<R, DIR>(&re[1][i * R], &im[1][i * R]);
         }
     } else {
-        const T *tr = twr + tw_offset(M, S), *ti = twi + tw_offset(M, S);
+        const V *tws = tw + tw_offset(M, S);
 #pragma unroll
         for (int i = 0; i < NJ; ++i) {
             const int q = threadIdx.x + i * THREADS;
             const int f = ffast ? (q % F) : (q / JPF);
             const int j = ffast ? (q / F) : (q % JPF);
             T *ra = &re[0][i * R], *ia = &im[0][i * R], *rb = &re[1][i * R], *ib = &im[1][i * R];
+            const V *pa = sd + f * RL + pad(j);
+            const V *pb = pa + F * RL;
 #pragma unroll
             for (int r = 0; r < R; ++r) {
-                const int ia_ = sidx<M>(f, j + r * JPF), ib_ = sidx<M>(F + f, j + r * JPF);
-                ra[r] = sre[ia_]; ia[r] = sim[ia_];
-                rb[r] = sre[ib_]; ib[r] = sim[ib_];
+                const V va = pa[pad(r * JPF)], vb = pb[pad(r * JPF)];
+                ra[r] = va.x; ia[r] = va.y;
+                rb[r] = vb.x; ib[r] = vb.y;
             }
             // W_{NS R}^{r k}, k = j mod NS, from this stage's table [(r-1) NS + k]
-            const int k = j % NS;
+            const V *tk = tws + (j % NS);
 #pragma unroll
             for (int r = 1; r < R; ++r) {
-                const T wr = tr[(r - 1) * NS + k];
-                const T wi = (DIR < 0) ? ti[(r - 1) * NS + k] : -ti[(r - 1) * NS + k];
+                const V w = tk[(r - 1) * NS];
+                const T wr = w.x, wi = (DIR < 0) ? w.y : -w.y;
                 T xr = ra[r] * wr - ia[r] * wi, xi = ra[r] * wi + ia[r] * wr;
                 ra[r] = xr; ia[r] = xi;
                 xr = rb[r] * wr - ib[r] * wi; xi = rb[r] * wi + ib[r] * wr;
@@ -201,59 +213,56 @@ __device__ __forceinline__ void run_stage(T (&re)[2][EH], T (&im)[2][EH], T *sre
             const int f = ffast ? (q % F) : (q / JPF);
             const int j = ffast ? (q / F) : (q % JPF);
             const int ob = (j / NS) * NS * R + (j % NS);
+            V *pa = sd + f * RL + pad(ob);
+            V *pb = pa + F * RL;
 #pragma unroll
             for (int r = 0; r < R; ++r) {
-                const int ia_ = sidx<M>(f, ob + r * NS), ib_ = sidx<M>(F + f, ob + r * NS);
-                sre[ia_] = re[0][i * R + r]; sim[ia_] = im[0][i * R + r];
-                sre[ib_] = re[1][i * R + r]; sim[ib_] = im[1][i * R + r];
+                pa[pad(r * NS)] = V{re[0][i * R + r], im[0][i * R + r]};
+                pb[pad(r * NS)] = V{re[1][i * R + r], im[1][i * R + r]};
             }
         }
         BAR::sync();
-        run_stage<T, M, F, EH, DIR, MAPF, S + 1, LD, ST, BAR, INPLACE>(re, im, sre, sim, twr, twi,
-                                                                         ld, st);
+        run_stage<T, M, F, EH, DIR, MAPF, S + 1, LD, ST, BAR, INPLACE>(re, im, sd, tw, ld, st);
     }
 }
 
 // Fills the per-stage twiddle tables from the forward table e^{-2 pi i k/M}:
 // stage s, entry (r-1) NS + k holds W_{NS R}^{r k} = W_M^{r k M/(NS R)}.
 template <typename T, int M, int THREADS, int S>
-__device__ __forceinline__ void fill_twiddles(T *twr, T *twi, const T *__restrict__ tw) {
+__device__ __forceinline__ void fill_twiddles(typename Vec2T<T>::type *tws, const T *__restrict__ tw) {
     if constexpr (S < n_stages(M)) {
         constexpr int R = stage_radix(M, S), NS = stage_ns(M, S);
         constexpr int n = (R - 1) * NS, off = tw_offset(M, S), step = M / (NS * R);
         for (int e = (int)threadIdx.x; e < n; e += THREADS) {
             const int r = e / NS + 1, k = e % NS;
             const int m = r * k * step;
-            twr[off + e] = tw[2 * m];
-            twi[off + e] = tw[2 * m + 1];
+            tws[off + e] = typename Vec2T<T>::type{tw[2 * m], tw[2 * m + 1]};
         }
-        fill_twiddles<T, M, THREADS, S + 1>(twr, twi, tw);
+        fill_twiddles<T, M, THREADS, S + 1>(tws, tw);
     }
 }
 
 // One tile whose input the Loader reads from shared memory that is then reused
 // in place for the stage exchanges (persistent kernels); twiddle tables filled.
 template <typename T, int M, int F, int EH, int DIR, bool MAPF, class BAR, class LD, class ST>
-__device__ __forceinline__ void run_tile_inplace(LD &ld, ST &st, T *buf, const T *twr,
-                                                 const T *twi) {
+__device__ __forceinline__ void run_tile_inplace(LD &ld, ST &st, typename Vec2T<T>::type *buf,
+                                                 const typename Vec2T<T>::type *tw) {
     T re[2][EH], im[2][EH];
-    run_stage<T, M, F, EH, DIR, MAPF, 0, LD, ST, BAR, true>(re, im, buf, buf + 2 * F * M, twr, twi,
-                                                            ld, st);
+    run_stage<T, M, F, EH, DIR, MAPF, 0, LD, ST, BAR, true>(re, im, buf, tw, ld, st);
 }
 
 // One pass over a tile.  tw: forward twiddles e^{-2 pi i k/M}, k < M, interleaved.
 template <typename T, int M, int F, int EH, int DIR, bool MAPF, class LD, class ST>
 __device__ __forceinline__ void run_pass(LD &ld, ST &st, const T *__restrict__ tw) {
+    using V = typename Vec2T<T>::type;
     constexpr int THREADS = F * M / EH;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    T *sre = reinterpret_cast<T *>(smem_raw);
-    T *sim = sre + 2 * F * M;
-    T *twr = sim + 2 * F * M;
-    T *twi = twr + (tw_words(M) > 0 ? tw_words(M) : 1);
+    V *sd = reinterpret_cast<V *>(smem_raw);
+    V *tws = reinterpret_cast<V *>(smem_raw + exch_bytes<T, M, F>());
     // made visible by the barrier that precedes the first shared-memory read
-    fill_twiddles<T, M, THREADS, 1>(twr, twi, tw);
+    fill_twiddles<T, M, THREADS, 1>(tws, tw);
     T re[2][EH], im[2][EH];
-    run_stage<T, M, F, EH, DIR, MAPF, 0>(re, im, sre, sim, twr, twi, ld, st);
+    run_stage<T, M, F, EH, DIR, MAPF, 0>(re, im, sd, tws, ld, st);
 }
 
 }  // namespace eng

@@ -404,7 +404,7 @@ int launch_geometry(const Plan &p, const BandDev &b, int64_t s0, int64_t ns, boo
     g.sky = p.sky;
     g.s0 = s0;
     g.w = p.w;
-    g.w_stride = p.n_max;
+    g.w_stride = p.w_stride;
     g.partials = p.partials;
     g.nblk = (int)blocks(b.n, 256);
     g.dbg_y = dbg_y;

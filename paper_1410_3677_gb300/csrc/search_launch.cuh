@@ -30,7 +30,7 @@ int launch_search_t(const Plan &p, int band_idx, const BandDev &b, int64_t s0, i
         ld1.w = reinterpret_cast<const W64 *>(p.w);
         ld1.chirp = p.chirp_d + (int64_t)band_idx * n_spin;
     }
-    ld1.w_stride = p.n_max;
+    ld1.w_stride = p.w_stride;
     ld1.n = (int)b.n;
     ld1.n_spin = n_spin;
     ld1.c0 = c0;

@@ -29,7 +29,8 @@ constexpr int kEH = 16;                    // complex elements per thread per tr
 constexpr int kETile = 2048;               // complex elements of one transform per tile
 constexpr int kNC = kETile / kEH;          // consumer threads (4 warps)
 constexpr int kThreads = kNC + 32;         // + one producer warp
-constexpr int kBufBytes = 2 * kETile * 8;  // two transforms of complex float
+// a staged tile (two transforms of complex float) or its padded exchange layout
+constexpr int kStageBytes = 2 * kETile * 8;
 constexpr uint64_t kWaitNs = 1000000000ull;
 
 template <int LOGN>
@@ -39,9 +40,13 @@ struct PC {
     static constexpr int F1 = kETile / N2;   // columns per pass-1 tile
     static constexpr int F2 = kETile / N1;   // rows per pass-2 tile
     static constexpr int T = N / kETile;     // tiles per cell and pass
-    static constexpr int TW1 = eng::tw_words(N2) > 0 ? eng::tw_words(N2) : 1;
-    static constexpr int TW2 = eng::tw_words(N1) > 0 ? eng::tw_words(N1) : 1;
-    static constexpr size_t SMEM = 2 * (size_t)kBufBytes + 4 * 2 * (size_t)(TW1 + TW2) + 64;
+    static constexpr int TW1 = eng::tw_entries(N2);
+    static constexpr int TW2 = eng::tw_entries(N1);
+    static constexpr int E1 = (int)eng::exch_bytes<float, N2, F1>();
+    static constexpr int E2 = (int)eng::exch_bytes<float, N1, F2>();
+    static constexpr int BUF = ((kStageBytes > E1 ? (kStageBytes > E2 ? kStageBytes : E2)
+                                                   : (E1 > E2 ? E1 : E2)) + 127) / 128 * 128;
+    static constexpr size_t SMEM = 2 * (size_t)BUF + 8 * (size_t)(TW1 + TW2) + 64;
     static_assert(F1 >= 1 && F2 >= 1 && F1 <= N1 && F2 <= N2, "tile shape");
     // Cfg-compatible views for the loaders/storers of passes.cuh
     struct C1 {
@@ -174,16 +179,14 @@ __global__ void __launch_bounds__(kThreads, 3) k_search_persistent(PArgs a) {
     using P = PC<LOGN>;
     extern __shared__ __align__(128) unsigned char smem[];
     unsigned char *bufs = smem;
-    float *tw1r = reinterpret_cast<float *>(smem + 2 * kBufBytes);
-    float *tw1i = tw1r + P::TW1;
-    float *tw2r = tw1i + P::TW1;
-    float *tw2i = tw2r + P::TW2;
-    uint64_t *full = reinterpret_cast<uint64_t *>(tw2i + P::TW2);   // 8-byte aligned: 2(TW1+TW2) floats precede
+    float2 *tw1 = reinterpret_cast<float2 *>(smem + 2 * P::BUF);
+    float2 *tw2 = tw1 + P::TW1;
+    uint64_t *full = reinterpret_cast<uint64_t *>(tw2 + P::TW2);
     uint64_t *empty = full + 2;
     ItemInfo *info = reinterpret_cast<ItemInfo *>(empty + 2);
 
-    eng::fill_twiddles<float, P::N2, kThreads, 1>(tw1r, tw1i, a.tw1);
-    eng::fill_twiddles<float, P::N1, kThreads, 1>(tw2r, tw2i, a.tw2);
+    eng::fill_twiddles<float, P::N2, kThreads, 1>(tw1, a.tw1);
+    eng::fill_twiddles<float, P::N1, kThreads, 1>(tw2, a.tw2);
     if (threadIdx.x == 0) {
         ptx::mbar_init(&full[0], 1);
         ptx::mbar_init(&full[1], 1);
@@ -239,8 +242,8 @@ __global__ void __launch_bounds__(kThreads, 3) k_search_persistent(PArgs a) {
             const int64_t cell = a.c_lo + (int64_t)batch * a.B + cib;
             const bool valid = cell < a.c_hi;
             uint32_t bytes = 0;
-            if (valid) bytes = kind == 1 ? (uint32_t)(a.rows * P::F1 * 16) : (uint32_t)kBufBytes;
-            unsigned char *dst = bufs + buf * kBufBytes;
+            if (valid) bytes = kind == 1 ? (uint32_t)(a.rows * P::F1 * 16) : (uint32_t)kStageBytes;
+            unsigned char *dst = bufs + buf * P::BUF;
             if (lane == 0) {
                 info[buf] = ItemInfo{kind, batch, tile, item};
                 ptx::mbar_arrive_expect_tx(&full[buf], bytes);
@@ -279,7 +282,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_search_persistent(PArgs a) {
         if (inf.kind == 0) break;
         const int cib = inf.tile / P::T, tic = inf.tile - cib * P::T;
         const int64_t cell = a.c_lo + (int64_t)inf.batch * a.B + cib;
-        float *bp = reinterpret_cast<float *>(bufs + buf * kBufBytes);
+        float2 *bp = reinterpret_cast<float2 *>(bufs + buf * P::BUF);
         if (cell < a.c_hi) {
             const int64_t sky = cell / a.n_spin;
             if (inf.kind == 1) {
@@ -299,7 +302,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_search_persistent(PArgs a) {
                 st.has_b = true;
                 st.k1_0 = tic * P::F1;
                 eng::run_tile_inplace<float, P::N2, P::F1, kEH, -1, true, eng::NamedBarrier<kNC>>(
-                    ld, st, bp, tw1r, tw1i);
+                    ld, st, bp, tw1);
             } else {
                 using C = typename P::C2;
                 StageLoadP2<C> ld;
@@ -316,7 +319,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_search_persistent(PArgs a) {
                 st.count = a.count;
                 st.cap = a.cap;
                 eng::run_tile_inplace<float, P::N1, P::F2, kEH, -1, false, eng::NamedBarrier<kNC>>(
-                    ld, st, bp, tw2r, tw2i);
+                    ld, st, bp, tw2);
             }
         }
         eng::NamedBarrier<kNC>::sync();   // the buffer is read, every store issued
