@@ -326,7 +326,12 @@ void create_impl(Plan &p, const fstat_plan_desc *d) {
         p.qerr = dalloc<uint32_t>(p, 1, n_alloc);
         check(cudaMemsetAsync(p.qerr, 0, sizeof(uint32_t), s), "memset");
         if (const char *v = getenv("FSTAT_TEST_WITHHOLD_ITEM")) p.withhold_item = atoll(v);
-        if (const char *v = getenv("FSTAT_BATCHED_LAUNCHES")) p.use_persistent = atoi(v) == 0;
+        if (const char *v = getenv("FSTAT_PERSISTENT")) p.use_persistent = atoi(v) != 0;
+        if (const char *v = getenv("FSTAT_TILE_THREADS")) p.tile_threads = atoi(v) == 128 ? 128 : 256;
+        if (const char *v = getenv("FSTAT_CELL_BATCH")) {
+            p.cell_batch = std::max(1, std::min(65535, atoi(v)));
+            scratch_bytes = std::max<size_t>(scratch_bytes, (size_t)p.cell_batch * 2 * max_nfft * tsz);
+        }
     }
     p.scratch = dalloc<unsigned char>(p, scratch_bytes, n_alloc);
     p.bw_elems = 2 * p.n_max + 2 * max_m;

@@ -97,7 +97,8 @@ struct Plan {
     uint32_t *queue = nullptr;     // [head | done1[nb] | done2[nb]]
     uint32_t *qerr = nullptr;      // error word (bit 0: a bounded wait ran out)
     int64_t withhold_item = -1;    // test hook (FSTAT_TEST_WITHHOLD_ITEM)
-    bool use_persistent = true;    // FSTAT_BATCHED_LAUNCHES=1: two launches per cell batch
+    bool use_persistent = false;   // FSTAT_PERSISTENT=1: one queue-fed launch per sky batch
+    int tile_threads = 256;        // FP32 batched passes: 128 or 256 threads per CTA
 
     // Bluestein / generic-FFT work buffers (double2)
     double *bw = nullptr;

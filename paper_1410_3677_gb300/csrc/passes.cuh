@@ -25,7 +25,8 @@ template <> struct Vec2<double> { using type = double2; };
 // (both 32 registers of payload per transform).
 template <typename T> constexpr int elems_per_thread() { return sizeof(T) == 4 ? 16 : 8; }
 
-template <typename T, int LOGN, int PASS>
+// TS: target threads per CTA (tile shape); smaller tiles give more, shorter CTAs per SM.
+template <typename T, int LOGN, int PASS, int TS = 256>
 struct Cfg {
     static constexpr int LOGN1 = LOGN / 2;
     static constexpr int LOGN2 = LOGN - LOGN / 2;
@@ -35,13 +36,13 @@ struct Cfg {
     static constexpr int M = PASS == 1 ? N2 : N1;         // length of this pass's FFTs
     static constexpr int OTHER = PASS == 1 ? N1 : N2;     // number of such FFTs
     static constexpr int EH = elems_per_thread<T>();
-    static constexpr int F0 = 256 * EH / M;
+    static constexpr int F0 = TS * EH / M;
     static constexpr int F = F0 < OTHER ? (F0 > 0 ? F0 : 1) : OTHER;   // sequences per tile
     static constexpr int THREADS = F * M / EH;
     static constexpr int TILES = OTHER / F;
     static constexpr size_t SMEM = eng::smem_bytes<T, M, F>();
-    // two resident CTAs per SM: at most 128 registers per thread at 256 threads
-    static constexpr int MIN_BLOCKS = THREADS >= 128 ? 2 : 1;
+    // 512 resident threads per SM: at most 128 registers per thread
+    static constexpr int MIN_BLOCKS = THREADS >= 256 ? 2 : (THREADS >= 128 ? 4 : 1);
     static_assert(THREADS >= 1 && THREADS <= 256, "tile shape");
 };
 
@@ -330,10 +331,10 @@ struct SearchEpi {
 };
 
 // ------------------------------------------------------------------ kernels
-template <typename T, int LOGN, int PASS, int DIR, bool MAPF, class LD, class ST>
-__global__ void __launch_bounds__(Cfg<T, LOGN, PASS>::THREADS, Cfg<T, LOGN, PASS>::MIN_BLOCKS)
+template <typename T, int LOGN, int PASS, int DIR, bool MAPF, class LD, class ST, int TS = 256>
+__global__ void __launch_bounds__(Cfg<T, LOGN, PASS, TS>::THREADS, Cfg<T, LOGN, PASS, TS>::MIN_BLOCKS)
 k_pass(LD ld, ST st, const T *__restrict__ tw) {
-    using C = Cfg<T, LOGN, PASS>;
+    using C = Cfg<T, LOGN, PASS, TS>;
     ld.init();
     st.init();
     eng::run_pass<T, C::M, C::F, C::EH, DIR, MAPF>(ld, st, tw);

@@ -8,11 +8,11 @@
 
 namespace fstat {
 
-template <typename T, int LOGN>
+template <typename T, int LOGN, int TS>
 int launch_search_t(const Plan &p, int band_idx, const BandDev &b, int64_t s0, int64_t c0,
                     int64_t nc, cudaStream_t s, cudaEvent_t mid) {
-    using C1 = Cfg<T, LOGN, 1>;
-    using C2 = Cfg<T, LOGN, 2>;
+    using C1 = Cfg<T, LOGN, 1, TS>;
+    using C2 = Cfg<T, LOGN, 2, TS>;
     using V = typename Vec2<T>::type;
     const TwiddleSet *tw = p.twiddles(LOGN);
     const T *tin1, *tin2, *tlo, *thi;
@@ -40,7 +40,7 @@ int launch_search_t(const Plan &p, int band_idx, const BandDev &b, int64_t s0, i
     st1.lo = tlo;
     st1.hi = thi;
     st1.n_tr = 2 * nc;
-    auto k1 = k_pass<T, LOGN, 1, -1, true, LD1, ST1>;
+    auto k1 = k_pass<T, LOGN, 1, -1, true, LD1, ST1, TS>;
     static bool attr1 = false;
     if (!attr1) { set_smem(k1, C1::SMEM); attr1 = true; }
     k1<<<dim3(C1::TILES, (unsigned)nc), C1::THREADS, C1::SMEM, s>>>(ld1, st1, tin2);
@@ -62,7 +62,7 @@ int launch_search_t(const Plan &p, int band_idx, const BandDev &b, int64_t s0, i
     st2.out = p.cand;
     st2.count = p.cand_count;
     st2.cap = (unsigned long long)p.cand_capacity;
-    auto k2 = k_pass<T, LOGN, 2, -1, false, LD2, ST2>;
+    auto k2 = k_pass<T, LOGN, 2, -1, false, LD2, ST2, TS>;
     static bool attr2 = false;
     if (!attr2) { set_smem(k2, C2::SMEM); attr2 = true; }
     k2<<<dim3(C2::TILES, (unsigned)nc), C2::THREADS, C2::SMEM, s>>>(ld2, st2, tin1);
@@ -73,19 +73,19 @@ template <typename T>
 int launch_search_dispatch(const Plan &p, int band_idx, const BandDev &b, int64_t s0, int64_t c0,
                            int64_t nc, cudaStream_t s, cudaEvent_t mid) {
     switch (b.logn) {
-        case 8: return launch_search_t<T, 8>(p, band_idx, b, s0, c0, nc, s, mid);
-        case 9: return launch_search_t<T, 9>(p, band_idx, b, s0, c0, nc, s, mid);
-        case 10: return launch_search_t<T, 10>(p, band_idx, b, s0, c0, nc, s, mid);
-        case 11: return launch_search_t<T, 11>(p, band_idx, b, s0, c0, nc, s, mid);
-        case 12: return launch_search_t<T, 12>(p, band_idx, b, s0, c0, nc, s, mid);
-        case 13: return launch_search_t<T, 13>(p, band_idx, b, s0, c0, nc, s, mid);
-        case 14: return launch_search_t<T, 14>(p, band_idx, b, s0, c0, nc, s, mid);
-        case 15: return launch_search_t<T, 15>(p, band_idx, b, s0, c0, nc, s, mid);
-        case 16: return launch_search_t<T, 16>(p, band_idx, b, s0, c0, nc, s, mid);
-        case 17: return launch_search_t<T, 17>(p, band_idx, b, s0, c0, nc, s, mid);
-        case 18: return launch_search_t<T, 18>(p, band_idx, b, s0, c0, nc, s, mid);
-        case 19: return launch_search_t<T, 19>(p, band_idx, b, s0, c0, nc, s, mid);
-        case 20: return launch_search_t<T, 20>(p, band_idx, b, s0, c0, nc, s, mid);
+        case 8: return p.tile_threads == 128 && sizeof(T) == 4 ? launch_search_t<T, 8, 128>(p, band_idx, b, s0, c0, nc, s, mid) : launch_search_t<T, 8, 256>(p, band_idx, b, s0, c0, nc, s, mid);
+        case 9: return p.tile_threads == 128 && sizeof(T) == 4 ? launch_search_t<T, 9, 128>(p, band_idx, b, s0, c0, nc, s, mid) : launch_search_t<T, 9, 256>(p, band_idx, b, s0, c0, nc, s, mid);
+        case 10: return p.tile_threads == 128 && sizeof(T) == 4 ? launch_search_t<T, 10, 128>(p, band_idx, b, s0, c0, nc, s, mid) : launch_search_t<T, 10, 256>(p, band_idx, b, s0, c0, nc, s, mid);
+        case 11: return p.tile_threads == 128 && sizeof(T) == 4 ? launch_search_t<T, 11, 128>(p, band_idx, b, s0, c0, nc, s, mid) : launch_search_t<T, 11, 256>(p, band_idx, b, s0, c0, nc, s, mid);
+        case 12: return p.tile_threads == 128 && sizeof(T) == 4 ? launch_search_t<T, 12, 128>(p, band_idx, b, s0, c0, nc, s, mid) : launch_search_t<T, 12, 256>(p, band_idx, b, s0, c0, nc, s, mid);
+        case 13: return p.tile_threads == 128 && sizeof(T) == 4 ? launch_search_t<T, 13, 128>(p, band_idx, b, s0, c0, nc, s, mid) : launch_search_t<T, 13, 256>(p, band_idx, b, s0, c0, nc, s, mid);
+        case 14: return p.tile_threads == 128 && sizeof(T) == 4 ? launch_search_t<T, 14, 128>(p, band_idx, b, s0, c0, nc, s, mid) : launch_search_t<T, 14, 256>(p, band_idx, b, s0, c0, nc, s, mid);
+        case 15: return p.tile_threads == 128 && sizeof(T) == 4 ? launch_search_t<T, 15, 128>(p, band_idx, b, s0, c0, nc, s, mid) : launch_search_t<T, 15, 256>(p, band_idx, b, s0, c0, nc, s, mid);
+        case 16: return p.tile_threads == 128 && sizeof(T) == 4 ? launch_search_t<T, 16, 128>(p, band_idx, b, s0, c0, nc, s, mid) : launch_search_t<T, 16, 256>(p, band_idx, b, s0, c0, nc, s, mid);
+        case 17: return p.tile_threads == 128 && sizeof(T) == 4 ? launch_search_t<T, 17, 128>(p, band_idx, b, s0, c0, nc, s, mid) : launch_search_t<T, 17, 256>(p, band_idx, b, s0, c0, nc, s, mid);
+        case 18: return p.tile_threads == 128 && sizeof(T) == 4 ? launch_search_t<T, 18, 128>(p, band_idx, b, s0, c0, nc, s, mid) : launch_search_t<T, 18, 256>(p, band_idx, b, s0, c0, nc, s, mid);
+        case 19: return p.tile_threads == 128 && sizeof(T) == 4 ? launch_search_t<T, 19, 128>(p, band_idx, b, s0, c0, nc, s, mid) : launch_search_t<T, 19, 256>(p, band_idx, b, s0, c0, nc, s, mid);
+        case 20: return p.tile_threads == 128 && sizeof(T) == 4 ? launch_search_t<T, 20, 128>(p, band_idx, b, s0, c0, nc, s, mid) : launch_search_t<T, 20, 256>(p, band_idx, b, s0, c0, nc, s, mid);
         default: return -1;
     }
 }

@@ -41,14 +41,17 @@ def _run(fs, w, thr, env=None, **kw):
     return p, rc, c, total
 
 
-@pytest.mark.parametrize("env", [{"FSTAT_PERSIST_BATCH": "1", "FSTAT_PERSIST_SLOTS": "2"},
-                                 {"FSTAT_PERSIST_BATCH": "3", "FSTAT_PERSIST_SLOTS": "3"},
-                                 {"FSTAT_PERSIST_BATCH": "5", "FSTAT_PERSIST_SLOTS": "8"}])
-def test_queue_matches_batched_launches_bitwise(fs, env):
-    """Tiny workload (N_fft = 2^13) and a two-sidereal-day band (2^18) with cell
+@pytest.mark.parametrize("env", [{"FSTAT_PERSISTENT": "1", "FSTAT_PERSIST_BATCH": "1", "FSTAT_PERSIST_SLOTS": "2"},
+                                 {"FSTAT_PERSISTENT": "1", "FSTAT_PERSIST_BATCH": "3", "FSTAT_PERSIST_SLOTS": "3"},
+                                 {"FSTAT_PERSISTENT": "1", "FSTAT_PERSIST_BATCH": "5", "FSTAT_PERSIST_SLOTS": "8"},
+                                 {"FSTAT_TILE_THREADS": "128"},
+                                 {"FSTAT_TILE_THREADS": "128", "FSTAT_CELL_BATCH": "7"}])
+def test_launch_shapes_match_bitwise(fs, env):
+    """The queue-fed persistent kernel and other tile / batch shapes against the
+    default two-launches-per-batch form.  Tiny workload (N_fft = 2^13) and a two-sidereal-day band (2^18) with cell
     counts that leave a partial last batch."""
     for w in (S.workload(1, n_sky=9, n_spin=3), S.workload(3, n_sky=5, n_spin=3)):
-        p0, rc0, ref, t0 = _run(fs, w, 8.0, {"FSTAT_BATCHED_LAUNCHES": "1"})
+        p0, rc0, ref, t0 = _run(fs, w, 8.0, {"FSTAT_PERSISTENT": "0"})
         p0.close()
         p1, rc1, got, t1 = _run(fs, w, 8.0, env)
         p1.close()
@@ -59,7 +62,7 @@ def test_queue_matches_batched_launches_bitwise(fs, env):
 def test_queue_cell_ranges(fs):
     """Ranges that start and end inside a sky position and a batch."""
     w = S.workload(1, n_sky=7, n_spin=5)
-    p, rc, full, _ = _run(fs, w, 6.0, {"FSTAT_PERSIST_BATCH": "4"})
+    p, rc, full, _ = _run(fs, w, 6.0, {"FSTAT_PERSISTENT": "1", "FSTAT_PERSIST_BATCH": "4"})
     parts = []
     for a, b in ((0, 3), (3, 17), (17, 35)):
         p.search(a, b)
@@ -71,7 +74,7 @@ def test_queue_cell_ranges(fs):
 def test_withheld_completion_times_out_and_gpu_stays_usable(fs):
     w = S.workload(1, n_sky=8, n_spin=4)
     t0 = time.time()
-    p, rc, _, _ = _run(fs, w, 20.0, {"FSTAT_TEST_WITHHOLD_ITEM": "0"})
+    p, rc, _, _ = _run(fs, w, 20.0, {"FSTAT_PERSISTENT": "1", "FSTAT_TEST_WITHHOLD_ITEM": "0"})
     elapsed = time.time() - t0
     assert rc == fs.FSTAT_ERR_TIMEOUT
     assert elapsed < 30.0
