@@ -303,6 +303,7 @@ void create_impl(Plan &p, const fstat_plan_desc *d) {
     const size_t w_elem = fp32 ? 16 : 32;
     p.w = dalloc<unsigned char>(p, (size_t)p.sky_batch * p.w_stride * w_elem, n_alloc);
     check(cudaMemsetAsync(p.w, 0, (size_t)p.sky_batch * p.w_stride * w_elem, s), "memset");
+    p.dbuf = dalloc<double>(p, (size_t)p.sky_batch * p.n_max, n_alloc);
     p.partials = dalloc<double>(p, std::max<int64_t>((int64_t)p.sky_batch * nblk * 3, 256), n_alloc);
     p.S = dalloc<double>(p, 3 * p.sky_batch, n_alloc);
     p.norm = dalloc<double>(p, 2 * p.sky_batch, n_alloc);
@@ -310,7 +311,8 @@ void create_impl(Plan &p, const fstat_plan_desc *d) {
     // FFT scratch: cell slots of 2 transforms; also hosts the generic FFT of the upsample
     const size_t tsz = fp32 ? sizeof(float2) : sizeof(double2);
     if (fp32) {
-        const int64_t budget = int64_t(64) << 20;
+        // launches of many cells amortise the partial last wave of each grid
+        const int64_t budget = int64_t(512) << 20;
         p.cell_batch = std::max<int64_t>(1, std::min<int64_t>(4096, budget / (2 * max_nfft * (int64_t)tsz)));
     } else {
         p.cell_batch = 1;

@@ -82,6 +82,7 @@ struct Plan {
     // per sky batch
     int64_t sky_batch = 0;
     void *w = nullptr;            // FP32: float4 [sky_batch][n_max]; FP64: double2 [2][n_max]
+    double *dbuf = nullptr;       // [sky_batch][n_max] per-sample delays
     double *partials = nullptr;   // [sky_batch][n_blocks_max][3]
     double *S = nullptr;          // [sky_batch][3]
     double *norm = nullptr;       // [sky_batch][2]: 1/(sigma^2 S_aa), 1/(sigma^2 S_bb)

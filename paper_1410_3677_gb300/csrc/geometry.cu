@@ -71,6 +71,8 @@ __global__ void k_sigma2_final(const double *__restrict__ partials, int nblk, in
 // ------------------------------------------------------------------ geometry
 struct GeoArgs {
     const double *r;
+    const double *d;          // per-sample delays of the sky batch, [sky][stride]
+    int64_t d_stride;
     const void *xu;
     int64_t m_up;
     int U;
@@ -95,15 +97,24 @@ __device__ __forceinline__ double delay_at(const double *__restrict__ r, const S
                      __dmul_rn(sc.nz, r[3 * j + 2]));
 }
 
-// Linear interpolation of the delay at fractional sample u; the end segments
-// extend beyond the data.
-__device__ __forceinline__ double delay_lin(const double *__restrict__ r, const SkyConst &sc,
-                                            int64_t n, double u) {
+// Linear interpolation of the delay at fractional sample u from the per-sample
+// delays dk; the end segments extend beyond the data.
+__device__ __forceinline__ double delay_lin(const double *__restrict__ dk, int64_t n, double u) {
     int64_t j = (int64_t)floor(u);
     j = j < 0 ? 0 : (j > n - 2 ? n - 2 : j);
     const double f = __dsub_rn(u, (double)j);
-    const double d0 = delay_at(r, sc, j), d1 = delay_at(r, sc, j + 1);
+    const double d0 = dk[j], d1 = dk[j + 1];
     return __dadd_rn(d0, __dmul_rn(f, __dsub_rn(d1, d0)));
+}
+
+// Roemer delay nhat . r_k of every sample of skies [s0, s0 + gridDim.y).
+__global__ void __launch_bounds__(256) k_delays(const double *__restrict__ r,
+                                                const SkyConst *__restrict__ sky, int64_t s0,
+                                                int64_t n, int64_t stride,
+                                                double *__restrict__ d) {
+    const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int sl = blockIdx.y;
+    if (k < n) d[(int64_t)sl * stride + k] = delay_at(r, sky[s0 + sl], k);
 }
 
 template <bool FP32>
@@ -115,11 +126,20 @@ __global__ void __launch_bounds__(256) k_geometry(GeoArgs g) {
     double saa = 0.0, sbb = 0.0, sab = 0.0;
     if (k < g.n) {
         // detector time t of barycentric sample k: t = k dt - d(k dt - d(k dt))
-        const double dk = delay_at(g.r, sc, k);
-        const double u0 = __dsub_rn((double)k, __ddiv_rn(dk, g.dt));
-        const double d1 = delay_lin(g.r, sc, g.n, u0);
-        const double u = __dsub_rn((double)k, __ddiv_rn(d1, g.dt));
-        const double d2 = delay_lin(g.r, sc, g.n, u);
+        const double *dd = g.d + (int64_t)sl * g.d_stride;
+        const double dk = dd[k];
+        double u0, d1, u, d2;
+        if constexpr (FP32) {     // reciprocal multiply: positions to ~1e-11 samples
+            u0 = (double)k - dk * g.inv_dt;
+            d1 = delay_lin(dd, g.n, u0);
+            u = (double)k - d1 * g.inv_dt;
+            d2 = delay_lin(dd, g.n, u);
+        } else {                  // the oracle's rounding sequence, for 1e-10 agreement of F
+            u0 = __dsub_rn((double)k, __ddiv_rn(dk, g.dt));
+            d1 = delay_lin(dd, g.n, u0);
+            u = __dsub_rn((double)k, __ddiv_rn(d1, g.dt));
+            d2 = delay_lin(dd, g.n, u);
+        }
         const bool valid = (u >= 0.0) && (u <= (double)(g.n - 1));
         const double t = u * g.dt;
         const double h = sc.alpha - (g.phi0 + kOmegaR * t);
@@ -393,6 +413,8 @@ int launch_geometry(const Plan &p, const BandDev &b, int64_t s0, int64_t ns, boo
                     cudaStream_t s) {
     GeoArgs g;
     g.r = b.r;
+    g.d = p.dbuf;
+    g.d_stride = p.n_max;
     g.xu = b.xu;
     g.U = p.desc.upsample;
     g.m_up = (int64_t)g.U * b.n;
@@ -412,9 +434,10 @@ int launch_geometry(const Plan &p, const BandDev &b, int64_t s0, int64_t ns, boo
     g.dbg_b = dbg_b;
     g.dbg_mask = dbg_mask;
     dim3 grid(g.nblk, (unsigned)ns);
+    k_delays<<<grid, 256, 0, s>>>(b.r, p.sky, s0, b.n, p.n_max, p.dbuf);
     if (fp32) k_geometry<true><<<grid, 256, 0, s>>>(g);
     else k_geometry<false><<<grid, 256, 0, s>>>(g);
-    return 1;
+    return 2;
 }
 
 int launch_reduce_norms(const Plan &p, const BandDev &b, int64_t ns, cudaStream_t s) {
