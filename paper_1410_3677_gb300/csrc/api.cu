@@ -301,23 +301,30 @@ void create_impl(Plan &p, const fstat_plan_desc *d) {
     const int64_t nblk = (p.n_max + 255) / 256;
     p.sky_batch = fp32 ? std::min<int64_t>(d->n_sky, 64) : 1;
     const size_t w_elem = fp32 ? 16 : 32;
-    p.w = dalloc<unsigned char>(p, (size_t)p.sky_batch * p.w_stride * w_elem, n_alloc);
-    check(cudaMemsetAsync(p.w, 0, (size_t)p.sky_batch * p.w_stride * w_elem, s), "memset");
+    for (int q = 0; q < 2; ++q) {
+        p.wbuf[q] = dalloc<unsigned char>(p, (size_t)p.sky_batch * p.w_stride * w_elem, n_alloc);
+        check(cudaMemsetAsync(p.wbuf[q], 0, (size_t)p.sky_batch * p.w_stride * w_elem, s), "memset");
+    }
     p.dbuf = dalloc<double>(p, (size_t)p.sky_batch * p.n_max, n_alloc);
     p.partials = dalloc<double>(p, std::max<int64_t>((int64_t)p.sky_batch * nblk * 3, 256), n_alloc);
     p.S = dalloc<double>(p, 3 * p.sky_batch, n_alloc);
-    p.norm = dalloc<double>(p, 2 * p.sky_batch, n_alloc);
+    for (int q = 0; q < 2; ++q) p.normbuf[q] = dalloc<double>(p, 2 * p.sky_batch, n_alloc);
 
     // FFT scratch: cell slots of 2 transforms; also hosts the generic FFT of the upsample
     const size_t tsz = fp32 ? sizeof(float2) : sizeof(double2);
     if (fp32) {
-        // launches of many cells amortise the partial last wave of each grid
-        const int64_t budget = int64_t(512) << 20;
+        // several worker streams, each running launch pairs of a batch of cells on its
+        // own scratch slot: one stream's partial last wave overlaps the next grids
+        p.n_workers = 3;
+        if (const char *v = getenv("FSTAT_STREAMS")) p.n_workers = std::max(1, std::min(8, atoi(v)));
+        const int64_t budget = int64_t(128) << 20;   // per worker slot
         p.cell_batch = std::max<int64_t>(1, std::min<int64_t>(4096, budget / (2 * max_nfft * (int64_t)tsz)));
+        if (const char *v = getenv("FSTAT_CELL_BATCH")) p.cell_batch = std::max(1, std::min(65535, atoi(v)));
     } else {
+        p.n_workers = 1;
         p.cell_batch = 1;
     }
-    size_t scratch_bytes = std::max<size_t>((size_t)p.cell_batch * 2 * max_nfft * tsz,
+    size_t scratch_bytes = std::max<size_t>((size_t)p.n_workers * p.cell_batch * 2 * max_nfft * tsz,
                                             (size_t)2 * std::max<int64_t>(max_m, p.n_max) * sizeof(double2) * 2);
     if (fp32) {
         if (const char *v = getenv("FSTAT_PERSIST_BATCH")) p.pbatch = std::max(1, atoi(v));
@@ -330,14 +337,34 @@ void create_impl(Plan &p, const fstat_plan_desc *d) {
         if (const char *v = getenv("FSTAT_TEST_WITHHOLD_ITEM")) p.withhold_item = atoll(v);
         if (const char *v = getenv("FSTAT_PERSISTENT")) p.use_persistent = atoi(v) != 0;
         if (const char *v = getenv("FSTAT_TILE_THREADS")) p.tile_threads = atoi(v) == 128 ? 128 : 256;
-        if (const char *v = getenv("FSTAT_CELL_BATCH")) {
-            p.cell_batch = std::max(1, std::min(65535, atoi(v)));
-            scratch_bytes = std::max<size_t>(scratch_bytes, (size_t)p.cell_batch * 2 * max_nfft * tsz);
-        }
     }
     p.scratch = dalloc<unsigned char>(p, scratch_bytes, n_alloc);
     p.bw_elems = 2 * p.n_max + 2 * max_m;
     p.bw = dalloc<double>(p, 2 * (size_t)std::max<int64_t>(p.bw_elems, 1), n_alloc);
+
+    // worker streams (the FP64 plain form runs on the plan's stream alone)
+    for (int q = 0; q < 2; ++q) {
+        check(cudaEventCreateWithFlags(&p.ev_geo[q], cudaEventDisableTiming), "event");
+        p.ev_all.push_back(p.ev_geo[q]);
+    }
+    for (int i = 0; i < p.n_workers; ++i) {
+        cudaStream_t ws = s;
+        if (p.n_workers > 1) {
+            check(cudaStreamCreateWithFlags(&ws, cudaStreamNonBlocking), "cudaStreamCreate");
+            p.own_workers.push_back(ws);
+        }
+        p.workers.push_back(ws);
+        for (int q = 0; q < 2; ++q) {
+            cudaEvent_t e;
+            check(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "event");
+            p.ev_all.push_back(e);
+            p.ev_done[q].push_back(e);
+        }
+        cudaEvent_t e;
+        check(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "event");
+        p.ev_all.push_back(e);
+        p.ev_join.push_back(e);
+    }
 
     p.cand_capacity = d->cand_capacity;
     p.cand = dalloc<CandRecord>(p, (size_t)p.cand_capacity, n_alloc);
@@ -353,6 +380,9 @@ void free_all(Plan &p) {
     p.allocs.clear();
     for (cudaEvent_t e : p.ev_all) cudaEventDestroy(e);
     p.ev_all.clear();
+    for (cudaStream_t w : p.own_workers) cudaStreamDestroy(w);
+    p.own_workers.clear();
+    p.workers.clear();
     p.ev_pool.clear();
     p.pending.clear();
     if (p.own_stream && p.stream) cudaStreamDestroy(p.stream);
@@ -428,12 +458,31 @@ void search_impl(Plan &p, int64_t begin, int64_t end) {
     check(cudaMemsetAsync(p.cand_count, 0, sizeof(unsigned long long), s), "memset");
     if (p.qerr) check(cudaMemsetAsync(p.qerr, 0, sizeof(uint32_t), s), "memset");
     const int64_t per_band = d.n_sky * d.n_spin;
+    const int NW = (int)p.workers.size();
+    const size_t slot_bytes = (size_t)p.cell_batch * 2 * (size_t)p.n_fft_max * (fp32 ? 8 : 16);
+    // the plan's stream waits for every worker stream
+    auto join_workers = [&]() {
+        if (NW < 2) return;
+        for (int i = 0; i < NW; ++i) {
+            check(cudaEventRecord(p.ev_join[i], p.workers[i]), "event");
+            check(cudaStreamWaitEvent(s, p.ev_join[i], 0), "stream wait");
+        }
+    };
+    // the worker streams start after everything queued so far on the plan's stream
+    {
+        check(cudaEventRecord(p.ev_geo[0], s), "event");
+        for (int i = 0; i < NW; ++i)
+            if (p.workers[i] != s) check(cudaStreamWaitEvent(p.workers[i], p.ev_geo[0], 0), "stream wait");
+    }
+    int64_t q = 0;        // sky batches so far (parity selects the w / norm buffers)
+    int64_t cbi = 0;      // cell batches so far (round-robin over the workers)
     for (int bi = 0; bi < d.n_bands; ++bi) {
         const int64_t b0 = (int64_t)bi * per_band;
         const int64_t lc0 = std::max<int64_t>(begin, b0) - b0;
         const int64_t lc1 = std::min<int64_t>(end, b0 + per_band) - b0;
         if (lc1 <= lc0) continue;
         BandDev &b = p.bands[bi];
+        join_workers();   // the prologue's transforms use the scratch area
         band_prologue(p, b);
         const int64_t s_first = lc0 / d.n_spin, s_last = (lc1 - 1) / d.n_spin;
         const double nfft = (double)b.n_fft;
@@ -443,28 +492,46 @@ void search_impl(Plan &p, int64_t begin, int64_t end) {
         const int i_p2 = stat_index(p, fp32 ? "fft_pass2_fstat_f32" : "fft_pass2_fstat_f64");
         const int i_pp = stat_index(p, "fft_fstat_persistent_f32");
         const double welem = fp32 ? 16.0 : 32.0;
-        for (int64_t sb = s_first; sb <= s_last; sb += p.sky_batch) {
+        for (int64_t sb = s_first; sb <= s_last; sb += p.sky_batch, ++q) {
+            const int par = (int)(q & 1);
             const int64_t ns = std::min<int64_t>(p.sky_batch, s_last + 1 - sb);
+            // the buffers of parity `par` were last read by the transforms of sky batch q - 2
+            if (q >= 2 && NW > 1)
+                for (int i = 0; i < NW; ++i)
+                    check(cudaStreamWaitEvent(s, p.ev_done[par][i], 0), "stream wait");
             // algorithmic bytes: ephemeris + upsampled series read, w written per sky
             const bool tg = stat_launch(p, i_geo, 0.0,
                                         (double)b.n * (24.0 + welem * ns) + (double)p.desc.upsample * b.n * (fp32 ? 4 : 8));
             cudaEvent_t g0 = nullptr, g1 = nullptr;
             if (tg) { g0 = ev_get(p); g1 = ev_get(p); check(cudaEventRecord(g0, s), "event"); }
-            p.launches += launch_geometry(p, b, sb, ns, fp32, nullptr, nullptr, nullptr, nullptr, s);
-            p.launches += launch_reduce_norms(p, b, ns, s);
+            p.launches += launch_geometry(p, b, sb, ns, fp32, p.wbuf[par], nullptr, nullptr, nullptr, nullptr, s);
+            p.launches += launch_reduce_norms(p, b, ns, p.normbuf[par], s);
             if (tg) { check(cudaEventRecord(g1, s), "event"); p.pending.push_back({i_geo, g0, g1}); }
             const int64_t c_lo = std::max<int64_t>(lc0, sb * d.n_spin);
             const int64_t c_hi = std::min<int64_t>(lc1, (sb + ns) * d.n_spin);
             if (fp32 && p.use_persistent && persistent_supported(b.logn)) {
+                join_workers();
                 const bool tp = stat_launch(p, i_pp, 2.0 * (c_hi - c_lo) * 5.0 * nfft * (lg1 + lg2),
                                             (double)ns * b.n * welem);
                 cudaEvent_t e0 = nullptr, e1 = nullptr;
                 if (tp) { e0 = ev_get(p); e1 = ev_get(p); check(cudaEventRecord(e0, s), "event"); }
-                p.launches += launch_search_persistent(p, bi, b, sb, c_lo, c_hi, s);
+                const CellBufs cbuf{p.wbuf[par], p.normbuf[par], p.scratch};
+                p.launches += launch_search_persistent(p, bi, b, sb, c_lo, c_hi, s, cbuf);
                 if (tp) { check(cudaEventRecord(e1, s), "event"); p.pending.push_back({i_pp, e0, e1}); }
+                if (NW > 1)
+                    for (int i = 0; i < NW; ++i) check(cudaEventRecord(p.ev_done[par][i], s), "event");
                 continue;
             }
-            for (int64_t c = c_lo; c < c_hi; c += p.cell_batch) {
+            if (NW > 1) {
+                check(cudaEventRecord(p.ev_geo[par], s), "event");
+                for (int i = 0; i < NW; ++i)
+                    check(cudaStreamWaitEvent(p.workers[i], p.ev_geo[par], 0), "stream wait");
+            }
+            for (int64_t c = c_lo; c < c_hi; c += p.cell_batch, ++cbi) {
+                const int wi = (int)(cbi % NW);
+                cudaStream_t ws = p.workers[wi];
+                const CellBufs cbuf{p.wbuf[par], p.normbuf[par],
+                                    static_cast<unsigned char *>(p.scratch) + wi * slot_bytes};
                 const int64_t nc = std::min<int64_t>(p.cell_batch, c_hi - c);
                 // 5 N log2 N per complex transform, split between the passes; two
                 // transforms per cell.  Pass 1 reads w once per distinct sky.
@@ -475,20 +542,23 @@ void search_impl(Plan &p, int64_t begin, int64_t end) {
                 cudaEvent_t e0 = nullptr, e1 = nullptr, e2 = nullptr;
                 if (t1) {
                     e0 = ev_get(p); e1 = ev_get(p); e2 = ev_get(p);
-                    check(cudaEventRecord(e0, s), "event");
+                    check(cudaEventRecord(e0, ws), "event");
                 }
-                const int L = fp32 ? launch_search_cells_f32(p, bi, b, sb, c, nc, s, e1)
-                                   : launch_search_cells_f64(p, bi, b, sb, c, nc, s, e1);
+                const int L = fp32 ? launch_search_cells_f32(p, bi, b, sb, c, nc, ws, e1, cbuf)
+                                   : launch_search_cells_f64(p, bi, b, sb, c, nc, ws, e1, cbuf);
                 if (L < 0) throw std::string("unsupported transform length");
                 p.launches += L;
                 if (t1) {
-                    check(cudaEventRecord(e2, s), "event");
+                    check(cudaEventRecord(e2, ws), "event");
                     p.pending.push_back({i_p1, e0, e1});
                     p.pending.push_back({i_p2, e1, e2});
                 }
             }
+            if (NW > 1)
+                for (int i = 0; i < NW; ++i) check(cudaEventRecord(p.ev_done[par][i], p.workers[i]), "event");
         }
     }
+    join_workers();
     check(cudaGetLastError(), "search launch");
     check(cudaStreamSynchronize(s), "search");
     collect_timing(p);
@@ -652,8 +722,8 @@ fstat_status fstat_debug_sky(fstat_plan *p, int band, int64_t sky, double *y, do
         }
         const bool fp32 = p->desc.form == FSTAT_FP32_BATCHED;
         band_prologue(*p, bd);
-        p->launches += launch_geometry(*p, bd, sky, 1, fp32, dy, da, db, dm, p->stream);
-        p->launches += launch_reduce_norms(*p, bd, 1, p->stream);
+        p->launches += launch_geometry(*p, bd, sky, 1, fp32, p->wbuf[0], dy, da, db, dm, p->stream);
+        p->launches += launch_reduce_norms(*p, bd, 1, p->normbuf[0], p->stream);
         check(cudaStreamSynchronize(p->stream), "debug sky");
         if (y) check(cudaMemcpy(y, dy, 2 * n * sizeof(double), cudaMemcpyDeviceToHost), "y");
         if (a) check(cudaMemcpy(a, da, n * sizeof(double), cudaMemcpyDeviceToHost), "a");

@@ -79,13 +79,14 @@ struct Plan {
     uint64_t *chirp_fx = nullptr;  // per (band, spin): frac(fdot dt^2 / 2) in 2^-64 cycles
     double *chirp_d = nullptr;     // per (band, spin): fdot dt^2 / 2 (FP64 form)
 
-    // per sky batch
+    // per sky batch (w and norm double-buffered by sky-batch parity so that the
+    // geometry of the next sky batch can overlap the transforms of this one)
     int64_t sky_batch = 0;
-    void *w = nullptr;            // FP32: float4 [sky_batch][n_max]; FP64: double2 [2][n_max]
+    void *wbuf[2] = {nullptr, nullptr};   // FP32: float4 [sky_batch][w_stride]; FP64: {y a, y b} double2 pairs
     double *dbuf = nullptr;       // [sky_batch][n_max] per-sample delays
     double *partials = nullptr;   // [sky_batch][n_blocks_max][3]
     double *S = nullptr;          // [sky_batch][3]
-    double *norm = nullptr;       // [sky_batch][2]: 1/(sigma^2 S_aa), 1/(sigma^2 S_bb)
+    double *normbuf[2] = {nullptr, nullptr};   // [sky_batch][2]: 1/(sigma^2 S_aa), 1/(sigma^2 S_bb)
     int64_t n_max = 0;
 
     // FFT scratch (cell slots)
@@ -99,6 +100,12 @@ struct Plan {
     uint32_t *qerr = nullptr;      // error word (bit 0: a bounded wait ran out)
     int64_t withhold_item = -1;    // test hook (FSTAT_TEST_WITHHOLD_ITEM)
     bool use_persistent = false;   // FSTAT_PERSISTENT=1: one queue-fed launch per sky batch
+    // worker streams of the batched FP32 passes, each with its own scratch slot
+    int n_workers = 1;
+    std::vector<cudaStream_t> workers, own_workers;
+    cudaEvent_t ev_geo[2] = {nullptr, nullptr};
+    std::vector<cudaEvent_t> ev_done[2];
+    std::vector<cudaEvent_t> ev_join;
     int tile_threads = 256;        // FP32 batched passes: 128 or 256 threads per CTA
 
     // Bluestein / generic-FFT work buffers (double2)
@@ -139,6 +146,13 @@ struct Plan {
     }
 };
 
+// Buffers one launch pair works on.
+struct CellBufs {
+    const void *w;
+    const double *norm;
+    void *scratch;
+};
+
 // ---------------------------------------------------------------- launchers
 // Each returns the number of kernels it launched (for the plan's counter).
 
@@ -166,11 +180,11 @@ int launch_upsample(const Plan &p, const BandDev &b, int U, void *xu, bool xu_fp
 // FP32 form writes w as float4 (y a, y b); FP64 form writes double2 wa, wb.
 // Optional diagnostics (nullptr to skip): y (double2), a, b (double), mask (uint8).
 int launch_geometry(const Plan &p, const BandDev &b, int64_t s0, int64_t ns, bool fp32,
-                    double *dbg_y, double *dbg_a, double *dbg_b, uint8_t *dbg_mask,
+                    void *w, double *dbg_y, double *dbg_a, double *dbg_b, uint8_t *dbg_mask,
                     cudaStream_t s);
 
 // Per-sky S sums and normalisations for the ns skies of the last geometry launch.
-int launch_reduce_norms(const Plan &p, const BandDev &b, int64_t ns, cudaStream_t s);
+int launch_reduce_norms(const Plan &p, const BandDev &b, int64_t ns, double *norm, cudaStream_t s);
 
 // The two FFT passes of the search for cells [c0, c0 + nc) of band `band_idx`
 // (cells of this band: c = sky * n_spin + spin, skies relative to sky base s0).
@@ -179,12 +193,14 @@ int launch_reduce_norms(const Plan &p, const BandDev &b, int64_t ns, cudaStream_
 bool persistent_supported(int logn);
 int persistent_tiles_per_cell(int logn);
 int launch_search_persistent(const Plan &p, int band_idx, const BandDev &b, int64_t s0,
-                             int64_t c_lo, int64_t c_hi, cudaStream_t s);
+                             int64_t c_lo, int64_t c_hi, cudaStream_t s, const CellBufs &cb);
 
 // `mid` (may be null) is recorded between the two passes.
 int launch_search_cells_f32(const Plan &p, int band_idx, const BandDev &b, int64_t s0,
-                            int64_t c0, int64_t nc, cudaStream_t s, cudaEvent_t mid);
+                            int64_t c0, int64_t nc, cudaStream_t s, cudaEvent_t mid,
+                            const CellBufs &cb);
 int launch_search_cells_f64(const Plan &p, int band_idx, const BandDev &b, int64_t s0,
-                            int64_t c0, int64_t nc, cudaStream_t s, cudaEvent_t mid);
+                            int64_t c0, int64_t nc, cudaStream_t s, cudaEvent_t mid,
+                            const CellBufs &cb);
 
 }  // namespace fstat

@@ -409,7 +409,7 @@ int launch_upsample(const Plan &p, const BandDev &b, int U, void *xu, bool xu_fp
 }
 
 int launch_geometry(const Plan &p, const BandDev &b, int64_t s0, int64_t ns, bool fp32,
-                    double *dbg_y, double *dbg_a, double *dbg_b, uint8_t *dbg_mask,
+                    void *w, double *dbg_y, double *dbg_a, double *dbg_b, uint8_t *dbg_mask,
                     cudaStream_t s) {
     GeoArgs g;
     g.r = b.r;
@@ -425,7 +425,7 @@ int launch_geometry(const Plan &p, const BandDev &b, int64_t s0, int64_t ns, boo
     g.phi0 = b.phi0;
     g.sky = p.sky;
     g.s0 = s0;
-    g.w = p.w;
+    g.w = w;
     g.w_stride = p.w_stride;
     g.partials = p.partials;
     g.nblk = (int)blocks(b.n, 256);
@@ -440,9 +440,9 @@ int launch_geometry(const Plan &p, const BandDev &b, int64_t s0, int64_t ns, boo
     return 2;
 }
 
-int launch_reduce_norms(const Plan &p, const BandDev &b, int64_t ns, cudaStream_t s) {
+int launch_reduce_norms(const Plan &p, const BandDev &b, int64_t ns, double *norm, cudaStream_t s) {
     k_reduce_norms<<<(unsigned)ns, 32, 0, s>>>(p.partials, (int)blocks(b.n, 256), b.sigma2, p.S,
-                                               p.norm);
+                                               norm);
     return 1;
 }
 

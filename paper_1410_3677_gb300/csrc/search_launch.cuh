@@ -10,7 +10,7 @@ namespace fstat {
 
 template <typename T, int LOGN, int TS>
 int launch_search_t(const Plan &p, int band_idx, const BandDev &b, int64_t s0, int64_t c0,
-                    int64_t nc, cudaStream_t s, cudaEvent_t mid) {
+                    int64_t nc, cudaStream_t s, cudaEvent_t mid, const CellBufs &cb) {
     using C1 = Cfg<T, LOGN, 1, TS>;
     using C2 = Cfg<T, LOGN, 2, TS>;
     using V = typename Vec2<T>::type;
@@ -24,10 +24,10 @@ int launch_search_t(const Plan &p, int band_idx, const BandDev &b, int64_t s0, i
     using ST1 = ScratchStore<T, C1, -1>;
     LD1 ld1{};
     if constexpr (sizeof(T) == 4) {
-        ld1.w = reinterpret_cast<const float4 *>(p.w);
+        ld1.w = reinterpret_cast<const float4 *>(cb.w);
         ld1.chirp = p.chirp_fx + (int64_t)band_idx * n_spin;
     } else {
-        ld1.w = reinterpret_cast<const W64 *>(p.w);
+        ld1.w = reinterpret_cast<const W64 *>(cb.w);
         ld1.chirp = p.chirp_d + (int64_t)band_idx * n_spin;
     }
     ld1.w_stride = p.w_stride;
@@ -36,7 +36,7 @@ int launch_search_t(const Plan &p, int band_idx, const BandDev &b, int64_t s0, i
     ld1.c0 = c0;
     ld1.s0 = s0;
     ST1 st1{};
-    st1.scratch = reinterpret_cast<V *>(p.scratch);
+    st1.scratch = reinterpret_cast<V *>(cb.scratch);
     st1.lo = tlo;
     st1.hi = thi;
     st1.n_tr = 2 * nc;
@@ -49,9 +49,9 @@ int launch_search_t(const Plan &p, int band_idx, const BandDev &b, int64_t s0, i
     using LD2 = ScratchLoad<T, C2>;
     using ST2 = SearchEpi<T, C2>;
     LD2 ld2{};
-    ld2.scratch = reinterpret_cast<const V *>(p.scratch);
+    ld2.scratch = reinterpret_cast<const V *>(cb.scratch);
     ST2 st2{};
-    st2.norm = p.norm;
+    st2.norm = cb.norm;
     st2.n_spin = n_spin;
     st2.c0 = c0;
     st2.s0 = s0;
@@ -71,21 +71,21 @@ int launch_search_t(const Plan &p, int band_idx, const BandDev &b, int64_t s0, i
 
 template <typename T>
 int launch_search_dispatch(const Plan &p, int band_idx, const BandDev &b, int64_t s0, int64_t c0,
-                           int64_t nc, cudaStream_t s, cudaEvent_t mid) {
+                           int64_t nc, cudaStream_t s, cudaEvent_t mid, const CellBufs &cb) {
     switch (b.logn) {
-        case 8: return p.tile_threads == 128 && sizeof(T) == 4 ? launch_search_t<T, 8, 128>(p, band_idx, b, s0, c0, nc, s, mid) : launch_search_t<T, 8, 256>(p, band_idx, b, s0, c0, nc, s, mid);
-        case 9: return p.tile_threads == 128 && sizeof(T) == 4 ? launch_search_t<T, 9, 128>(p, band_idx, b, s0, c0, nc, s, mid) : launch_search_t<T, 9, 256>(p, band_idx, b, s0, c0, nc, s, mid);
-        case 10: return p.tile_threads == 128 && sizeof(T) == 4 ? launch_search_t<T, 10, 128>(p, band_idx, b, s0, c0, nc, s, mid) : launch_search_t<T, 10, 256>(p, band_idx, b, s0, c0, nc, s, mid);
-        case 11: return p.tile_threads == 128 && sizeof(T) == 4 ? launch_search_t<T, 11, 128>(p, band_idx, b, s0, c0, nc, s, mid) : launch_search_t<T, 11, 256>(p, band_idx, b, s0, c0, nc, s, mid);
-        case 12: return p.tile_threads == 128 && sizeof(T) == 4 ? launch_search_t<T, 12, 128>(p, band_idx, b, s0, c0, nc, s, mid) : launch_search_t<T, 12, 256>(p, band_idx, b, s0, c0, nc, s, mid);
-        case 13: return p.tile_threads == 128 && sizeof(T) == 4 ? launch_search_t<T, 13, 128>(p, band_idx, b, s0, c0, nc, s, mid) : launch_search_t<T, 13, 256>(p, band_idx, b, s0, c0, nc, s, mid);
-        case 14: return p.tile_threads == 128 && sizeof(T) == 4 ? launch_search_t<T, 14, 128>(p, band_idx, b, s0, c0, nc, s, mid) : launch_search_t<T, 14, 256>(p, band_idx, b, s0, c0, nc, s, mid);
-        case 15: return p.tile_threads == 128 && sizeof(T) == 4 ? launch_search_t<T, 15, 128>(p, band_idx, b, s0, c0, nc, s, mid) : launch_search_t<T, 15, 256>(p, band_idx, b, s0, c0, nc, s, mid);
-        case 16: return p.tile_threads == 128 && sizeof(T) == 4 ? launch_search_t<T, 16, 128>(p, band_idx, b, s0, c0, nc, s, mid) : launch_search_t<T, 16, 256>(p, band_idx, b, s0, c0, nc, s, mid);
-        case 17: return p.tile_threads == 128 && sizeof(T) == 4 ? launch_search_t<T, 17, 128>(p, band_idx, b, s0, c0, nc, s, mid) : launch_search_t<T, 17, 256>(p, band_idx, b, s0, c0, nc, s, mid);
-        case 18: return p.tile_threads == 128 && sizeof(T) == 4 ? launch_search_t<T, 18, 128>(p, band_idx, b, s0, c0, nc, s, mid) : launch_search_t<T, 18, 256>(p, band_idx, b, s0, c0, nc, s, mid);
-        case 19: return p.tile_threads == 128 && sizeof(T) == 4 ? launch_search_t<T, 19, 128>(p, band_idx, b, s0, c0, nc, s, mid) : launch_search_t<T, 19, 256>(p, band_idx, b, s0, c0, nc, s, mid);
-        case 20: return p.tile_threads == 128 && sizeof(T) == 4 ? launch_search_t<T, 20, 128>(p, band_idx, b, s0, c0, nc, s, mid) : launch_search_t<T, 20, 256>(p, band_idx, b, s0, c0, nc, s, mid);
+        case 8: return p.tile_threads == 128 && sizeof(T) == 4 ? launch_search_t<T, 8, 128>(p, band_idx, b, s0, c0, nc, s, mid, cb) : launch_search_t<T, 8, 256>(p, band_idx, b, s0, c0, nc, s, mid, cb);
+        case 9: return p.tile_threads == 128 && sizeof(T) == 4 ? launch_search_t<T, 9, 128>(p, band_idx, b, s0, c0, nc, s, mid, cb) : launch_search_t<T, 9, 256>(p, band_idx, b, s0, c0, nc, s, mid, cb);
+        case 10: return p.tile_threads == 128 && sizeof(T) == 4 ? launch_search_t<T, 10, 128>(p, band_idx, b, s0, c0, nc, s, mid, cb) : launch_search_t<T, 10, 256>(p, band_idx, b, s0, c0, nc, s, mid, cb);
+        case 11: return p.tile_threads == 128 && sizeof(T) == 4 ? launch_search_t<T, 11, 128>(p, band_idx, b, s0, c0, nc, s, mid, cb) : launch_search_t<T, 11, 256>(p, band_idx, b, s0, c0, nc, s, mid, cb);
+        case 12: return p.tile_threads == 128 && sizeof(T) == 4 ? launch_search_t<T, 12, 128>(p, band_idx, b, s0, c0, nc, s, mid, cb) : launch_search_t<T, 12, 256>(p, band_idx, b, s0, c0, nc, s, mid, cb);
+        case 13: return p.tile_threads == 128 && sizeof(T) == 4 ? launch_search_t<T, 13, 128>(p, band_idx, b, s0, c0, nc, s, mid, cb) : launch_search_t<T, 13, 256>(p, band_idx, b, s0, c0, nc, s, mid, cb);
+        case 14: return p.tile_threads == 128 && sizeof(T) == 4 ? launch_search_t<T, 14, 128>(p, band_idx, b, s0, c0, nc, s, mid, cb) : launch_search_t<T, 14, 256>(p, band_idx, b, s0, c0, nc, s, mid, cb);
+        case 15: return p.tile_threads == 128 && sizeof(T) == 4 ? launch_search_t<T, 15, 128>(p, band_idx, b, s0, c0, nc, s, mid, cb) : launch_search_t<T, 15, 256>(p, band_idx, b, s0, c0, nc, s, mid, cb);
+        case 16: return p.tile_threads == 128 && sizeof(T) == 4 ? launch_search_t<T, 16, 128>(p, band_idx, b, s0, c0, nc, s, mid, cb) : launch_search_t<T, 16, 256>(p, band_idx, b, s0, c0, nc, s, mid, cb);
+        case 17: return p.tile_threads == 128 && sizeof(T) == 4 ? launch_search_t<T, 17, 128>(p, band_idx, b, s0, c0, nc, s, mid, cb) : launch_search_t<T, 17, 256>(p, band_idx, b, s0, c0, nc, s, mid, cb);
+        case 18: return p.tile_threads == 128 && sizeof(T) == 4 ? launch_search_t<T, 18, 128>(p, band_idx, b, s0, c0, nc, s, mid, cb) : launch_search_t<T, 18, 256>(p, band_idx, b, s0, c0, nc, s, mid, cb);
+        case 19: return p.tile_threads == 128 && sizeof(T) == 4 ? launch_search_t<T, 19, 128>(p, band_idx, b, s0, c0, nc, s, mid, cb) : launch_search_t<T, 19, 256>(p, band_idx, b, s0, c0, nc, s, mid, cb);
+        case 20: return p.tile_threads == 128 && sizeof(T) == 4 ? launch_search_t<T, 20, 128>(p, band_idx, b, s0, c0, nc, s, mid, cb) : launch_search_t<T, 20, 256>(p, band_idx, b, s0, c0, nc, s, mid, cb);
         default: return -1;
     }
 }

@@ -335,7 +335,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_search_persistent(PArgs a) {
 
 template <int LOGN>
 int launch_t(const Plan &p, int band_idx, const BandDev &b, int64_t s0, int64_t c_lo,
-             int64_t c_hi, cudaStream_t s) {
+             int64_t c_hi, cudaStream_t s, const CellBufs &cb) {
     using P = PC<LOGN>;
     static int grid = 0;
     auto k = k_search_persistent<LOGN>;
@@ -349,7 +349,7 @@ int launch_t(const Plan &p, int band_idx, const BandDev &b, int64_t s0, int64_t 
     }
     const TwiddleSet *tw = p.twiddles(LOGN);
     PArgs a;
-    a.w = reinterpret_cast<const float4 *>(p.w);
+    a.w = reinterpret_cast<const float4 *>(cb.w);
     a.w_stride = p.w_stride;
     a.n = (int)b.n;
     a.rows = (int)((b.n + P::N1 - 1) / P::N1);
@@ -361,12 +361,12 @@ int launch_t(const Plan &p, int band_idx, const BandDev &b, int64_t s0, int64_t 
     a.B = (int)p.pbatch;
     a.S = (int)p.pslots;
     a.nb = (int)((c_hi - c_lo + a.B - 1) / a.B);
-    a.scratch = reinterpret_cast<float2 *>(p.scratch);
+    a.scratch = reinterpret_cast<float2 *>(cb.scratch);
     a.tw1 = tw->in2_f;
     a.tw2 = tw->in1_f;
     a.lo = tw->lo_f;
     a.hi = tw->hi_f;
-    a.norm = p.norm;
+    a.norm = cb.norm;
     a.cell_base = (uint32_t)((int64_t)band_idx * p.desc.n_sky * p.desc.n_spin);
     a.bin_lo = b.lo;
     a.bin_hi = b.hi;
@@ -391,17 +391,17 @@ bool persistent_supported(int logn) { return logn >= 12 && logn <= 20; }
 int persistent_tiles_per_cell(int logn) { return (1 << logn) / kETile; }
 
 int launch_search_persistent(const Plan &p, int band_idx, const BandDev &b, int64_t s0,
-                             int64_t c_lo, int64_t c_hi, cudaStream_t s) {
+                             int64_t c_lo, int64_t c_hi, cudaStream_t s, const CellBufs &cb) {
     switch (b.logn) {
-        case 12: return launch_t<12>(p, band_idx, b, s0, c_lo, c_hi, s);
-        case 13: return launch_t<13>(p, band_idx, b, s0, c_lo, c_hi, s);
-        case 14: return launch_t<14>(p, band_idx, b, s0, c_lo, c_hi, s);
-        case 15: return launch_t<15>(p, band_idx, b, s0, c_lo, c_hi, s);
-        case 16: return launch_t<16>(p, band_idx, b, s0, c_lo, c_hi, s);
-        case 17: return launch_t<17>(p, band_idx, b, s0, c_lo, c_hi, s);
-        case 18: return launch_t<18>(p, band_idx, b, s0, c_lo, c_hi, s);
-        case 19: return launch_t<19>(p, band_idx, b, s0, c_lo, c_hi, s);
-        case 20: return launch_t<20>(p, band_idx, b, s0, c_lo, c_hi, s);
+        case 12: return launch_t<12>(p, band_idx, b, s0, c_lo, c_hi, s, cb);
+        case 13: return launch_t<13>(p, band_idx, b, s0, c_lo, c_hi, s, cb);
+        case 14: return launch_t<14>(p, band_idx, b, s0, c_lo, c_hi, s, cb);
+        case 15: return launch_t<15>(p, band_idx, b, s0, c_lo, c_hi, s, cb);
+        case 16: return launch_t<16>(p, band_idx, b, s0, c_lo, c_hi, s, cb);
+        case 17: return launch_t<17>(p, band_idx, b, s0, c_lo, c_hi, s, cb);
+        case 18: return launch_t<18>(p, band_idx, b, s0, c_lo, c_hi, s, cb);
+        case 19: return launch_t<19>(p, band_idx, b, s0, c_lo, c_hi, s, cb);
+        case 20: return launch_t<20>(p, band_idx, b, s0, c_lo, c_hi, s, cb);
         default: return -1;
     }
 }
