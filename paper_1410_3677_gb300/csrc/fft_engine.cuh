@@ -22,6 +22,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 namespace fstat {
 namespace eng {
 
@@ -126,14 +128,45 @@ struct NamedBarrier {
     }
 };
 
+// Synchronises the TPF threads that share one sequence in the per-warp mapping:
+// the warp when TPF <= 32, else a named barrier per group (ids 1 ..).
+template <int TPF>
+struct GroupBarrier {
+    __device__ __forceinline__ static void sync() {
+        if constexpr (TPF <= 32) {
+            __syncwarp();
+        } else {
+            asm volatile("bar.sync %0, %1;" ::"r"(1 + (int)threadIdx.x / TPF), "n"(TPF) : "memory");
+        }
+    }
+};
+
+// Job mappings (which sequence f and butterfly j a thread's i-th job of a stage is):
+//   kMapJ   consecutive threads take consecutive butterflies, sequences interleave
+//           across warps (CTA-wide barriers);
+//   kMapFJ  as kMapJ, but the first and last stage take consecutive sequences
+//           (columns of a strided tile, for coalesced global access);
+//   kMapW   the TPF = M/EH threads of a group own one sequence for all stages, so
+//           only the group synchronises (warps run out of phase).
+constexpr int kMapJ = 0, kMapFJ = 1, kMapW = 2;
+
+template <int MAPM, int S, int NST, int F, int JPF, int TPF, int THREADS>
+__device__ __forceinline__ void job_fj(int i, int &f, int &j) {
+    if constexpr (MAPM == kMapW) {
+        f = (int)threadIdx.x / TPF;
+        j = (int)threadIdx.x % TPF + TPF * i;
+    } else {
+        const int q = (int)threadIdx.x + i * THREADS;
+        constexpr bool ffast = MAPM == kMapFJ && (S == 0 || S == NST - 1);
+        f = ffast ? (q % F) : (q / JPF);
+        j = ffast ? (q / F) : (q % JPF);
+    }
+}
+
 // ------------------------------------------------------------------ the pass
-// MAPF: first and last stage map consecutive threads to consecutive sequences
-// (f fastest) -- used where the Loader/Storer walk a strided column tile, so that
-// a warp's global accesses cover contiguous columns.  Middle stages always map
-// consecutive threads to consecutive butterflies of one sequence.
 // INPLACE: the Loader reads shared memory that the stage-0 scatter overwrites,
 // so the scatter waits for every thread's gather.
-template <typename T, int M, int F, int EH, int DIR, bool MAPF, int S, class LD, class ST,
+template <typename T, int M, int F, int EH, int DIR, int MAPM, int S, class LD, class ST,
           class BAR = CtaBarrier, bool INPLACE = false>
 __device__ __forceinline__ void run_stage(T (&re)[2][EH], T (&im)[2][EH],
                                           typename Vec2T<T>::type *sd,
@@ -146,16 +179,16 @@ __device__ __forceinline__ void run_stage(T (&re)[2][EH], T (&im)[2][EH],
     constexpr int JPF = M / R;
     constexpr int THREADS = F * M / EH;
     constexpr int RL = row_ld(M);
-    constexpr bool ffast = MAPF && (S == 0 || S == NST - 1);
+    constexpr int TPF = M / EH;
+    using SB = std::conditional_t<MAPM == kMapW, GroupBarrier<TPF>, BAR>;
     static_assert(EH % R == 0, "elements per thread must be a multiple of the radix");
 
     if constexpr (S == 0) {
         // every load of the tile is issued before any arithmetic
 #pragma unroll
         for (int i = 0; i < NJ; ++i) {
-            const int q = threadIdx.x + i * THREADS;
-            const int f = ffast ? (q % F) : (q / JPF);
-            const int j = ffast ? (q / F) : (q % JPF);
+            int f, j;
+            job_fj<MAPM, S, NST, F, JPF, TPF, THREADS>(i, f, j);
             ld.template load<R, JPF>(f, j, &re[0][i * R], &im[0][i * R], &re[1][i * R],
                                      &im[1][i * R]);
         }
@@ -168,9 +201,8 @@ __device__ __forceinline__ void run_stage(T (&re)[2][EH], T (&im)[2][EH],
         const V *tws = tw + tw_offset(M, S);
 #pragma unroll
         for (int i = 0; i < NJ; ++i) {
-            const int q = threadIdx.x + i * THREADS;
-            const int f = ffast ? (q % F) : (q / JPF);
-            const int j = ffast ? (q / F) : (q % JPF);
+            int f, j;
+            job_fj<MAPM, S, NST, F, JPF, TPF, THREADS>(i, f, j);
             T *ra = &re[0][i * R], *ia = &im[0][i * R], *rb = &re[1][i * R], *ib = &im[1][i * R];
             const V *pa = sd + f * RL + pad(j);
             const V *pb = pa + F * RL;
@@ -199,19 +231,17 @@ __device__ __forceinline__ void run_stage(T (&re)[2][EH], T (&im)[2][EH],
     if constexpr (S == NST - 1) {
 #pragma unroll
         for (int i = 0; i < NJ; ++i) {
-            const int q = threadIdx.x + i * THREADS;
-            const int f = ffast ? (q % F) : (q / JPF);
-            const int j = ffast ? (q / F) : (q % JPF);
+            int f, j;
+            job_fj<MAPM, S, NST, F, JPF, TPF, THREADS>(i, f, j);
             st.template store<R, JPF>(f, j, &re[0][i * R], &im[0][i * R], &re[1][i * R],
                                       &im[1][i * R]);
         }
     } else {
-        if constexpr (S > 0 || INPLACE) BAR::sync();   // every read of this stage is done
+        if constexpr (S > 0 || INPLACE) SB::sync();   // every read of this stage is done
 #pragma unroll
         for (int i = 0; i < NJ; ++i) {
-            const int q = threadIdx.x + i * THREADS;
-            const int f = ffast ? (q % F) : (q / JPF);
-            const int j = ffast ? (q / F) : (q % JPF);
+            int f, j;
+            job_fj<MAPM, S, NST, F, JPF, TPF, THREADS>(i, f, j);
             const int ob = (j / NS) * NS * R + (j % NS);
             V *pa = sd + f * RL + pad(ob);
             V *pb = pa + F * RL;
@@ -221,8 +251,8 @@ __device__ __forceinline__ void run_stage(T (&re)[2][EH], T (&im)[2][EH],
                 pb[pad(r * NS)] = V{re[1][i * R + r], im[1][i * R + r]};
             }
         }
-        BAR::sync();
-        run_stage<T, M, F, EH, DIR, MAPF, S + 1, LD, ST, BAR, INPLACE>(re, im, sd, tw, ld, st);
+        SB::sync();
+        run_stage<T, M, F, EH, DIR, MAPM, S + 1, LD, ST, BAR, INPLACE>(re, im, sd, tw, ld, st);
     }
 }
 
@@ -244,25 +274,27 @@ __device__ __forceinline__ void fill_twiddles(typename Vec2T<T>::type *tws, cons
 
 // One tile whose input the Loader reads from shared memory that is then reused
 // in place for the stage exchanges (persistent kernels); twiddle tables filled.
-template <typename T, int M, int F, int EH, int DIR, bool MAPF, class BAR, class LD, class ST>
+template <typename T, int M, int F, int EH, int DIR, int MAPM, class BAR, class LD, class ST>
 __device__ __forceinline__ void run_tile_inplace(LD &ld, ST &st, typename Vec2T<T>::type *buf,
                                                  const typename Vec2T<T>::type *tw) {
     T re[2][EH], im[2][EH];
-    run_stage<T, M, F, EH, DIR, MAPF, 0, LD, ST, BAR, true>(re, im, buf, tw, ld, st);
+    run_stage<T, M, F, EH, DIR, MAPM, 0, LD, ST, BAR, true>(re, im, buf, tw, ld, st);
 }
 
 // One pass over a tile.  tw: forward twiddles e^{-2 pi i k/M}, k < M, interleaved.
-template <typename T, int M, int F, int EH, int DIR, bool MAPF, class LD, class ST>
+template <typename T, int M, int F, int EH, int DIR, int MAPM, class LD, class ST>
 __device__ __forceinline__ void run_pass(LD &ld, ST &st, const T *__restrict__ tw) {
     using V = typename Vec2T<T>::type;
     constexpr int THREADS = F * M / EH;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     V *sd = reinterpret_cast<V *>(smem_raw);
     V *tws = reinterpret_cast<V *>(smem_raw + exch_bytes<T, M, F>());
-    // made visible by the barrier that precedes the first shared-memory read
     fill_twiddles<T, M, THREADS, 1>(tws, tw);
+    // with CTA-wide stage barriers the first one publishes the tables; groups that
+    // synchronise only among themselves need a CTA barrier here
+    if constexpr (MAPM == kMapW && n_stages(M) > 1) __syncthreads();
     T re[2][EH], im[2][EH];
-    run_stage<T, M, F, EH, DIR, MAPF, 0>(re, im, sd, tws, ld, st);
+    run_stage<T, M, F, EH, DIR, MAPM, 0>(re, im, sd, tws, ld, st);
 }
 
 }  // namespace eng

@@ -27,7 +27,7 @@ int generic_t(const TwiddleSet &tw, const void *in, void *out, int64_t ntr, void
     st1.lo = tlo;
     st1.hi = thi;
     st1.n_tr = ntr;
-    auto k1 = k_pass<T, LOGN, 1, DIR, true, GenericLoad<T, C1>, ScratchStore<T, C1, DIR>>;
+    auto k1 = k_pass<T, LOGN, 1, DIR, eng::kMapFJ, GenericLoad<T, C1>, ScratchStore<T, C1, DIR>>;
     static bool a1 = false;
     if (!a1) { set_smem(k1, C1::SMEM); a1 = true; }
     k1<<<dim3(C1::TILES, pairs), C1::THREADS, C1::SMEM, s>>>(ld1, st1, tin2);
@@ -37,7 +37,7 @@ int generic_t(const TwiddleSet &tw, const void *in, void *out, int64_t ntr, void
     GenericStore<T, C2> st2{};
     st2.out = reinterpret_cast<V *>(out);
     st2.n_tr = ntr;
-    auto k2 = k_pass<T, LOGN, 2, DIR, false, ScratchLoad<T, C2>, GenericStore<T, C2>>;
+    auto k2 = k_pass<T, LOGN, 2, DIR, eng::kMapJ, ScratchLoad<T, C2>, GenericStore<T, C2>>;
     static bool a2 = false;
     if (!a2) { set_smem(k2, C2::SMEM); a2 = true; }
     k2<<<dim3(C2::TILES, pairs), C2::THREADS, C2::SMEM, s>>>(ld2, st2, tin1);

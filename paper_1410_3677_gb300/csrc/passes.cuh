@@ -116,13 +116,17 @@ struct SearchLoadF32 {
 #pragma unroll
         for (int r = 0; r < R; ++r) {
             const uint32_t k = (uint32_t)(k1_0 + f + C::N1 * (j + r * JPF));
-            const uint64_t kk = (uint64_t)k * (uint64_t)k;
-            const int32_t top = (int32_t)((afx * kk) >> 32);          // cycles in [-1/2, 1/2)
-            const float ph = (float)top * 1.4629180792671596e-09f;    // 2 pi / 2^32
-            float s, c;
-            __sincosf(ph, &s, &c);
-            ra[r] = v[r].x * c + v[r].y * s; ia[r] = v[r].y * c - v[r].x * s;
-            rb[r] = v[r].z * c + v[r].w * s; ib[r] = v[r].w * c - v[r].z * s;
+            if (k < (uint32_t)n) {        // the zero padding needs no phase
+                const uint64_t kk = (uint64_t)k * (uint64_t)k;
+                const int32_t top = (int32_t)((afx * kk) >> 32);          // cycles in [-1/2, 1/2)
+                const float ph = (float)top * 1.4629180792671596e-09f;    // 2 pi / 2^32
+                float s, c;
+                __sincosf(ph, &s, &c);
+                ra[r] = v[r].x * c + v[r].y * s; ia[r] = v[r].y * c - v[r].x * s;
+                rb[r] = v[r].z * c + v[r].w * s; ib[r] = v[r].w * c - v[r].z * s;
+            } else {
+                ra[r] = 0.f; ia[r] = 0.f; rb[r] = 0.f; ib[r] = 0.f;
+            }
         }
     }
 };
@@ -331,13 +335,65 @@ struct SearchEpi {
 };
 
 // ------------------------------------------------------------------ kernels
-template <typename T, int LOGN, int PASS, int DIR, bool MAPF, class LD, class ST, int TS = 256>
+template <typename T, int LOGN, int PASS, int DIR, int MAPM, class LD, class ST, int TS = 256>
 __global__ void __launch_bounds__(Cfg<T, LOGN, PASS, TS>::THREADS, Cfg<T, LOGN, PASS, TS>::MIN_BLOCKS)
 k_pass(LD ld, ST st, const T *__restrict__ tw) {
     using C = Cfg<T, LOGN, PASS, TS>;
     ld.init();
     st.init();
-    eng::run_pass<T, C::M, C::F, C::EH, DIR, MAPF>(ld, st, tw);
+    eng::run_pass<T, C::M, C::F, C::EH, DIR, MAPM>(ld, st, tw);
+}
+
+// Pass-1 output parked in the exchange area, in natural order, one row per
+// sequence (the group that transformed a column writes only its own row).
+template <typename T, class C>
+struct RowParkStore {
+    using V = typename Vec2<T>::type;
+    V *sd;
+    template <int R, int JPF>
+    __device__ __forceinline__ void store(int f, int j, T *ra, T *ia, T *rb, T *ib) const {
+        constexpr int RL = eng::row_ld(C::M);
+        V *pa = sd + f * RL, *pb = sd + (C::F + f) * RL;
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int l2 = j + r * JPF;
+            pa[eng::pad(l2)] = V{ra[r], ia[r]};
+            pb[eng::pad(l2)] = V{rb[r], ib[r]};
+        }
+    }
+};
+
+// Search pass 1 with one sequence per thread group: each group gathers its
+// column, demodulates and transforms it with group-local synchronisation only,
+// parks the result in its shared-memory row; then the CTA writes the tile to
+// scratch row by row (coalesced), applying the inter-pass twiddle
+// W_N^{k1 l2} = hi[m >> log N1] lo[m & (N1 - 1)], m = k1 l2.
+template <typename T, int LOGN, int TS, class LD>
+__global__ void __launch_bounds__(Cfg<T, LOGN, 1, TS>::THREADS, Cfg<T, LOGN, 1, TS>::MIN_BLOCKS)
+k_search_pass1(LD ld, typename Vec2<T>::type *scratch, const T *__restrict__ lo,
+               const T *__restrict__ hi, const T *__restrict__ tw) {
+    using C = Cfg<T, LOGN, 1, TS>;
+    using V = typename Vec2<T>::type;
+    constexpr int RL = eng::row_ld(C::M);
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    V *sd = reinterpret_cast<V *>(smem_raw);
+    ld.init();
+    RowParkStore<T, C> st{sd};
+    eng::run_pass<T, C::M, C::F, C::EH, -1, eng::kMapW>(ld, st, tw);
+    __syncthreads();
+    V *base = scratch + (int64_t)blockIdx.y * 2 * C::N;
+    const int k1_0 = blockIdx.x * C::F;
+    for (int idx = threadIdx.x; idx < C::F * C::M; idx += C::THREADS) {
+        const int l2 = idx / C::F, f = idx - l2 * C::F;
+        const int k1 = k1_0 + f;
+        const int m = k1 * l2;
+        const V th = __ldg(reinterpret_cast<const V *>(hi) + (m >> C::LOGN1));
+        const V tl = __ldg(reinterpret_cast<const V *>(lo) + (m & (C::N1 - 1)));
+        const T wr = th.x * tl.x - th.y * tl.y, wi = th.x * tl.y + th.y * tl.x;
+        const V a = sd[f * RL + eng::pad(l2)], b = sd[(C::F + f) * RL + eng::pad(l2)];
+        base[(int64_t)l2 * C::N1 + k1] = V{a.x * wr - a.y * wi, a.x * wi + a.y * wr};
+        base[C::N + (int64_t)l2 * C::N1 + k1] = V{b.x * wr - b.y * wi, b.x * wi + b.y * wr};
+    }
 }
 
 template <class KernelPtr>

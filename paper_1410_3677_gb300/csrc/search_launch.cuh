@@ -21,7 +21,6 @@ int launch_search_t(const Plan &p, int band_idx, const BandDev &b, int64_t s0, i
     const int n_spin = (int)p.desc.n_spin;
 
     using LD1 = std::conditional_t<sizeof(T) == 4, SearchLoadF32<C1>, SearchLoadF64<C1>>;
-    using ST1 = ScratchStore<T, C1, -1>;
     LD1 ld1{};
     if constexpr (sizeof(T) == 4) {
         ld1.w = reinterpret_cast<const float4 *>(cb.w);
@@ -35,15 +34,11 @@ int launch_search_t(const Plan &p, int band_idx, const BandDev &b, int64_t s0, i
     ld1.n_spin = n_spin;
     ld1.c0 = c0;
     ld1.s0 = s0;
-    ST1 st1{};
-    st1.scratch = reinterpret_cast<V *>(cb.scratch);
-    st1.lo = tlo;
-    st1.hi = thi;
-    st1.n_tr = 2 * nc;
-    auto k1 = k_pass<T, LOGN, 1, -1, true, LD1, ST1, TS>;
+    auto k1 = k_search_pass1<T, LOGN, TS, LD1>;
     static bool attr1 = false;
     if (!attr1) { set_smem(k1, C1::SMEM); attr1 = true; }
-    k1<<<dim3(C1::TILES, (unsigned)nc), C1::THREADS, C1::SMEM, s>>>(ld1, st1, tin2);
+    k1<<<dim3(C1::TILES, (unsigned)nc), C1::THREADS, C1::SMEM, s>>>(
+        ld1, reinterpret_cast<V *>(cb.scratch), tlo, thi, tin2);
     if (mid) cudaEventRecord(mid, s);
 
     using LD2 = ScratchLoad<T, C2>;
@@ -62,7 +57,7 @@ int launch_search_t(const Plan &p, int band_idx, const BandDev &b, int64_t s0, i
     st2.out = p.cand;
     st2.count = p.cand_count;
     st2.cap = (unsigned long long)p.cand_capacity;
-    auto k2 = k_pass<T, LOGN, 2, -1, false, LD2, ST2, TS>;
+    auto k2 = k_pass<T, LOGN, 2, -1, eng::kMapW, LD2, ST2, TS>;
     static bool attr2 = false;
     if (!attr2) { set_smem(k2, C2::SMEM); attr2 = true; }
     k2<<<dim3(C2::TILES, (unsigned)nc), C2::THREADS, C2::SMEM, s>>>(ld2, st2, tin1);

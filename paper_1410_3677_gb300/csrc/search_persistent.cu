@@ -301,7 +301,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_search_persistent(PArgs a) {
                 st.base = a.scratch + ((int64_t)(inf.batch % a.S) * a.B + cib) * 2 * P::N;
                 st.has_b = true;
                 st.k1_0 = tic * P::F1;
-                eng::run_tile_inplace<float, P::N2, P::F1, kEH, -1, true, eng::NamedBarrier<kNC>>(
+                eng::run_tile_inplace<float, P::N2, P::F1, kEH, -1, eng::kMapFJ, eng::NamedBarrier<kNC>>(
                     ld, st, bp, tw1);
             } else {
                 using C = typename P::C2;
@@ -318,7 +318,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_search_persistent(PArgs a) {
                 st.out = a.out;
                 st.count = a.count;
                 st.cap = a.cap;
-                eng::run_tile_inplace<float, P::N1, P::F2, kEH, -1, false, eng::NamedBarrier<kNC>>(
+                eng::run_tile_inplace<float, P::N1, P::F2, kEH, -1, eng::kMapJ, eng::NamedBarrier<kNC>>(
                     ld, st, bp, tw2);
             }
         }
