@@ -336,7 +336,7 @@ void create_impl(Plan &p, const fstat_plan_desc *d) {
         check(cudaMemsetAsync(p.qerr, 0, sizeof(uint32_t), s), "memset");
         if (const char *v = getenv("FSTAT_TEST_WITHHOLD_ITEM")) p.withhold_item = atoll(v);
         if (const char *v = getenv("FSTAT_PERSISTENT")) p.use_persistent = atoi(v) != 0;
-        if (const char *v = getenv("FSTAT_TILE_THREADS")) p.tile_threads = atoi(v) == 128 ? 128 : 256;
+        if (const char *v = getenv("FSTAT_ELEMS_PER_THREAD")) p.elems_per_thread = atoi(v) == 8 ? 8 : 16;
     }
     p.scratch = dalloc<unsigned char>(p, scratch_bytes, n_alloc);
     p.bw_elems = 2 * p.n_max + 2 * max_m;

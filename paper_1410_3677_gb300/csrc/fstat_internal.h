@@ -106,7 +106,7 @@ struct Plan {
     cudaEvent_t ev_geo[2] = {nullptr, nullptr};
     std::vector<cudaEvent_t> ev_done[2];
     std::vector<cudaEvent_t> ev_join;
-    int tile_threads = 256;        // FP32 batched passes: 128 or 256 threads per CTA
+    int elems_per_thread = 16;     // FP32 batched passes: 16 or 8 complex elements per thread
 
     // Bluestein / generic-FFT work buffers (double2)
     double *bw = nullptr;

@@ -25,8 +25,10 @@ template <> struct Vec2<double> { using type = double2; };
 // (both 32 registers of payload per transform).
 template <typename T> constexpr int elems_per_thread() { return sizeof(T) == 4 ? 16 : 8; }
 
-// TS: target threads per CTA (tile shape); smaller tiles give more, shorter CTAs per SM.
-template <typename T, int LOGN, int PASS, int TS = 256>
+// TS: target threads per CTA (tile shape); EHT: complex elements per thread per
+// transform (0: the default for T).  Fewer elements per thread mean fewer
+// registers and more resident warps.
+template <typename T, int LOGN, int PASS, int TS = 256, int EHT = 0>
 struct Cfg {
     static constexpr int LOGN1 = LOGN / 2;
     static constexpr int LOGN2 = LOGN - LOGN / 2;
@@ -35,14 +37,16 @@ struct Cfg {
     static constexpr int N = 1 << LOGN;
     static constexpr int M = PASS == 1 ? N2 : N1;         // length of this pass's FFTs
     static constexpr int OTHER = PASS == 1 ? N1 : N2;     // number of such FFTs
-    static constexpr int EH = elems_per_thread<T>();
+    static constexpr int EH = EHT > 0 ? EHT : elems_per_thread<T>();
     static constexpr int F0 = TS * EH / M;
     static constexpr int F = F0 < OTHER ? (F0 > 0 ? F0 : 1) : OTHER;   // sequences per tile
     static constexpr int THREADS = F * M / EH;
     static constexpr int TILES = OTHER / F;
     static constexpr size_t SMEM = eng::smem_bytes<T, M, F>();
-    // 512 resident threads per SM: at most 128 registers per thread
-    static constexpr int MIN_BLOCKS = THREADS >= 256 ? 2 : (THREADS >= 128 ? 4 : 1);
+    // resident threads per SM: 512 at 16 (FP32) / 8 (FP64) elements per thread
+    // (<= 128 registers), 1024 at 8 FP32 elements (<= 64 registers)
+    static constexpr int RES = (EH * (int)sizeof(T) <= 32) ? 1024 : 512;
+    static constexpr int MIN_BLOCKS = THREADS >= 64 ? (RES / THREADS < 8 ? RES / THREADS : 8) : 1;
     static_assert(THREADS >= 1 && THREADS <= 256, "tile shape");
 };
 
@@ -335,10 +339,12 @@ struct SearchEpi {
 };
 
 // ------------------------------------------------------------------ kernels
-template <typename T, int LOGN, int PASS, int DIR, int MAPM, class LD, class ST, int TS = 256>
-__global__ void __launch_bounds__(Cfg<T, LOGN, PASS, TS>::THREADS, Cfg<T, LOGN, PASS, TS>::MIN_BLOCKS)
+template <typename T, int LOGN, int PASS, int DIR, int MAPM, class LD, class ST, int TS = 256,
+          int EHT = 0>
+__global__ void __launch_bounds__(Cfg<T, LOGN, PASS, TS, EHT>::THREADS,
+                                  Cfg<T, LOGN, PASS, TS, EHT>::MIN_BLOCKS)
 k_pass(LD ld, ST st, const T *__restrict__ tw) {
-    using C = Cfg<T, LOGN, PASS, TS>;
+    using C = Cfg<T, LOGN, PASS, TS, EHT>;
     ld.init();
     st.init();
     eng::run_pass<T, C::M, C::F, C::EH, DIR, MAPM>(ld, st, tw);

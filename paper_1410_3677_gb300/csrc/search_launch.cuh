@@ -8,11 +8,11 @@
 
 namespace fstat {
 
-template <typename T, int LOGN, int TS>
+template <typename T, int LOGN, int TS, int EHT>
 int launch_search_t(const Plan &p, int band_idx, const BandDev &b, int64_t s0, int64_t c0,
                     int64_t nc, cudaStream_t s, cudaEvent_t mid, const CellBufs &cb) {
-    using C1 = Cfg<T, LOGN, 1, TS>;
-    using C2 = Cfg<T, LOGN, 2, TS>;
+    using C1 = Cfg<T, LOGN, 1, TS, EHT>;
+    using C2 = Cfg<T, LOGN, 2, TS, EHT>;
     using V = typename Vec2<T>::type;
     const TwiddleSet *tw = p.twiddles(LOGN);
     const T *tin1, *tin2, *tlo, *thi;
@@ -34,11 +34,16 @@ int launch_search_t(const Plan &p, int band_idx, const BandDev &b, int64_t s0, i
     ld1.n_spin = n_spin;
     ld1.c0 = c0;
     ld1.s0 = s0;
-    auto k1 = k_search_pass1<T, LOGN, TS, LD1>;
+    using ST1 = ScratchStore<T, C1, -1>;
+    ST1 st1{};
+    st1.scratch = reinterpret_cast<V *>(cb.scratch);
+    st1.lo = tlo;
+    st1.hi = thi;
+    st1.n_tr = 2 * nc;
+    auto k1 = k_pass<T, LOGN, 1, -1, eng::kMapFJ, LD1, ST1, TS, EHT>;
     static bool attr1 = false;
     if (!attr1) { set_smem(k1, C1::SMEM); attr1 = true; }
-    k1<<<dim3(C1::TILES, (unsigned)nc), C1::THREADS, C1::SMEM, s>>>(
-        ld1, reinterpret_cast<V *>(cb.scratch), tlo, thi, tin2);
+    k1<<<dim3(C1::TILES, (unsigned)nc), C1::THREADS, C1::SMEM, s>>>(ld1, st1, tin2);
     if (mid) cudaEventRecord(mid, s);
 
     using LD2 = ScratchLoad<T, C2>;
@@ -57,7 +62,7 @@ int launch_search_t(const Plan &p, int band_idx, const BandDev &b, int64_t s0, i
     st2.out = p.cand;
     st2.count = p.cand_count;
     st2.cap = (unsigned long long)p.cand_capacity;
-    auto k2 = k_pass<T, LOGN, 2, -1, eng::kMapW, LD2, ST2, TS>;
+    auto k2 = k_pass<T, LOGN, 2, -1, eng::kMapW, LD2, ST2, TS, EHT>;
     static bool attr2 = false;
     if (!attr2) { set_smem(k2, C2::SMEM); attr2 = true; }
     k2<<<dim3(C2::TILES, (unsigned)nc), C2::THREADS, C2::SMEM, s>>>(ld2, st2, tin1);
@@ -68,19 +73,19 @@ template <typename T>
 int launch_search_dispatch(const Plan &p, int band_idx, const BandDev &b, int64_t s0, int64_t c0,
                            int64_t nc, cudaStream_t s, cudaEvent_t mid, const CellBufs &cb) {
     switch (b.logn) {
-        case 8: return p.tile_threads == 128 && sizeof(T) == 4 ? launch_search_t<T, 8, 128>(p, band_idx, b, s0, c0, nc, s, mid, cb) : launch_search_t<T, 8, 256>(p, band_idx, b, s0, c0, nc, s, mid, cb);
-        case 9: return p.tile_threads == 128 && sizeof(T) == 4 ? launch_search_t<T, 9, 128>(p, band_idx, b, s0, c0, nc, s, mid, cb) : launch_search_t<T, 9, 256>(p, band_idx, b, s0, c0, nc, s, mid, cb);
-        case 10: return p.tile_threads == 128 && sizeof(T) == 4 ? launch_search_t<T, 10, 128>(p, band_idx, b, s0, c0, nc, s, mid, cb) : launch_search_t<T, 10, 256>(p, band_idx, b, s0, c0, nc, s, mid, cb);
-        case 11: return p.tile_threads == 128 && sizeof(T) == 4 ? launch_search_t<T, 11, 128>(p, band_idx, b, s0, c0, nc, s, mid, cb) : launch_search_t<T, 11, 256>(p, band_idx, b, s0, c0, nc, s, mid, cb);
-        case 12: return p.tile_threads == 128 && sizeof(T) == 4 ? launch_search_t<T, 12, 128>(p, band_idx, b, s0, c0, nc, s, mid, cb) : launch_search_t<T, 12, 256>(p, band_idx, b, s0, c0, nc, s, mid, cb);
-        case 13: return p.tile_threads == 128 && sizeof(T) == 4 ? launch_search_t<T, 13, 128>(p, band_idx, b, s0, c0, nc, s, mid, cb) : launch_search_t<T, 13, 256>(p, band_idx, b, s0, c0, nc, s, mid, cb);
-        case 14: return p.tile_threads == 128 && sizeof(T) == 4 ? launch_search_t<T, 14, 128>(p, band_idx, b, s0, c0, nc, s, mid, cb) : launch_search_t<T, 14, 256>(p, band_idx, b, s0, c0, nc, s, mid, cb);
-        case 15: return p.tile_threads == 128 && sizeof(T) == 4 ? launch_search_t<T, 15, 128>(p, band_idx, b, s0, c0, nc, s, mid, cb) : launch_search_t<T, 15, 256>(p, band_idx, b, s0, c0, nc, s, mid, cb);
-        case 16: return p.tile_threads == 128 && sizeof(T) == 4 ? launch_search_t<T, 16, 128>(p, band_idx, b, s0, c0, nc, s, mid, cb) : launch_search_t<T, 16, 256>(p, band_idx, b, s0, c0, nc, s, mid, cb);
-        case 17: return p.tile_threads == 128 && sizeof(T) == 4 ? launch_search_t<T, 17, 128>(p, band_idx, b, s0, c0, nc, s, mid, cb) : launch_search_t<T, 17, 256>(p, band_idx, b, s0, c0, nc, s, mid, cb);
-        case 18: return p.tile_threads == 128 && sizeof(T) == 4 ? launch_search_t<T, 18, 128>(p, band_idx, b, s0, c0, nc, s, mid, cb) : launch_search_t<T, 18, 256>(p, band_idx, b, s0, c0, nc, s, mid, cb);
-        case 19: return p.tile_threads == 128 && sizeof(T) == 4 ? launch_search_t<T, 19, 128>(p, band_idx, b, s0, c0, nc, s, mid, cb) : launch_search_t<T, 19, 256>(p, band_idx, b, s0, c0, nc, s, mid, cb);
-        case 20: return p.tile_threads == 128 && sizeof(T) == 4 ? launch_search_t<T, 20, 128>(p, band_idx, b, s0, c0, nc, s, mid, cb) : launch_search_t<T, 20, 256>(p, band_idx, b, s0, c0, nc, s, mid, cb);
+        case 8: return p.elems_per_thread == 8 && sizeof(T) == 4 ? launch_search_t<T, 8, 256, 8>(p, band_idx, b, s0, c0, nc, s, mid, cb) : launch_search_t<T, 8, 256, 0>(p, band_idx, b, s0, c0, nc, s, mid, cb);
+        case 9: return p.elems_per_thread == 8 && sizeof(T) == 4 ? launch_search_t<T, 9, 256, 8>(p, band_idx, b, s0, c0, nc, s, mid, cb) : launch_search_t<T, 9, 256, 0>(p, band_idx, b, s0, c0, nc, s, mid, cb);
+        case 10: return p.elems_per_thread == 8 && sizeof(T) == 4 ? launch_search_t<T, 10, 256, 8>(p, band_idx, b, s0, c0, nc, s, mid, cb) : launch_search_t<T, 10, 256, 0>(p, band_idx, b, s0, c0, nc, s, mid, cb);
+        case 11: return p.elems_per_thread == 8 && sizeof(T) == 4 ? launch_search_t<T, 11, 256, 8>(p, band_idx, b, s0, c0, nc, s, mid, cb) : launch_search_t<T, 11, 256, 0>(p, band_idx, b, s0, c0, nc, s, mid, cb);
+        case 12: return p.elems_per_thread == 8 && sizeof(T) == 4 ? launch_search_t<T, 12, 256, 8>(p, band_idx, b, s0, c0, nc, s, mid, cb) : launch_search_t<T, 12, 256, 0>(p, band_idx, b, s0, c0, nc, s, mid, cb);
+        case 13: return p.elems_per_thread == 8 && sizeof(T) == 4 ? launch_search_t<T, 13, 256, 8>(p, band_idx, b, s0, c0, nc, s, mid, cb) : launch_search_t<T, 13, 256, 0>(p, band_idx, b, s0, c0, nc, s, mid, cb);
+        case 14: return p.elems_per_thread == 8 && sizeof(T) == 4 ? launch_search_t<T, 14, 256, 8>(p, band_idx, b, s0, c0, nc, s, mid, cb) : launch_search_t<T, 14, 256, 0>(p, band_idx, b, s0, c0, nc, s, mid, cb);
+        case 15: return p.elems_per_thread == 8 && sizeof(T) == 4 ? launch_search_t<T, 15, 256, 8>(p, band_idx, b, s0, c0, nc, s, mid, cb) : launch_search_t<T, 15, 256, 0>(p, band_idx, b, s0, c0, nc, s, mid, cb);
+        case 16: return p.elems_per_thread == 8 && sizeof(T) == 4 ? launch_search_t<T, 16, 256, 8>(p, band_idx, b, s0, c0, nc, s, mid, cb) : launch_search_t<T, 16, 256, 0>(p, band_idx, b, s0, c0, nc, s, mid, cb);
+        case 17: return p.elems_per_thread == 8 && sizeof(T) == 4 ? launch_search_t<T, 17, 256, 8>(p, band_idx, b, s0, c0, nc, s, mid, cb) : launch_search_t<T, 17, 256, 0>(p, band_idx, b, s0, c0, nc, s, mid, cb);
+        case 18: return p.elems_per_thread == 8 && sizeof(T) == 4 ? launch_search_t<T, 18, 256, 8>(p, band_idx, b, s0, c0, nc, s, mid, cb) : launch_search_t<T, 18, 256, 0>(p, band_idx, b, s0, c0, nc, s, mid, cb);
+        case 19: return p.elems_per_thread == 8 && sizeof(T) == 4 ? launch_search_t<T, 19, 256, 8>(p, band_idx, b, s0, c0, nc, s, mid, cb) : launch_search_t<T, 19, 256, 0>(p, band_idx, b, s0, c0, nc, s, mid, cb);
+        case 20: return p.elems_per_thread == 8 && sizeof(T) == 4 ? launch_search_t<T, 20, 256, 8>(p, band_idx, b, s0, c0, nc, s, mid, cb) : launch_search_t<T, 20, 256, 0>(p, band_idx, b, s0, c0, nc, s, mid, cb);
         default: return -1;
     }
 }

@@ -44,8 +44,8 @@ def _run(fs, w, thr, env=None, **kw):
 @pytest.mark.parametrize("env", [{"FSTAT_PERSISTENT": "1", "FSTAT_PERSIST_BATCH": "1", "FSTAT_PERSIST_SLOTS": "2"},
                                  {"FSTAT_PERSISTENT": "1", "FSTAT_PERSIST_BATCH": "3", "FSTAT_PERSIST_SLOTS": "3"},
                                  {"FSTAT_PERSISTENT": "1", "FSTAT_PERSIST_BATCH": "5", "FSTAT_PERSIST_SLOTS": "8"},
-                                 {"FSTAT_TILE_THREADS": "128"},
-                                 {"FSTAT_TILE_THREADS": "128", "FSTAT_CELL_BATCH": "7"}])
+                                 {"FSTAT_ELEMS_PER_THREAD": "8"},
+                                 {"FSTAT_ELEMS_PER_THREAD": "8", "FSTAT_CELL_BATCH": "7", "FSTAT_STREAMS": "2"}])
 def test_launch_shapes_match_bitwise(fs, env):
     """The queue-fed persistent kernel and other tile / batch shapes against the
     default two-launches-per-batch form.  Tiny workload (N_fft = 2^13) and a two-sidereal-day band (2^18) with cell
