@@ -179,6 +179,37 @@ fstat_status fstat_plan_set_timing(fstat_plan *plan, int sample_every);
 fstat_status fstat_plan_kernel_stats(const fstat_plan *plan, fstat_kernel_stat *out, int cap,
                                      int *n);
 
+/* Allocation-free F of one cell (the paper has no counterpart: this entry point
+   exists for callers that cannot allocate device memory -- for example a host
+   application that reserves the whole device memory budget up front and hands
+   libraries only views of it, or code that must not pay for an allocation while it
+   runs).  It evaluates, without any cudaMalloc, the FP32 zero-padded transforms and
+   F = |F_a|^2 norm_a + |F_b|^2 norm_b for every bin in [bin_lo, bin_hi] of one
+   (sky, spindown) cell, from the resampled, phase-demodulated series of that sky:
+     w      device pointer, w[4 k .. 4 k + 3] = (Re y_k a_k, Im y_k a_k, Re y_k b_k,
+            Im y_k b_k), k < n (the FP32 form's per-sky series; zero outside the
+            resampled window);
+     n_fft  power of two, 2^12 <= n_fft <= 2^18 (the maximum), n_fft >= 2 n;
+     chirp_rate  fdot dt^2 / 2 (cycles per sample^2), |chirp_rate| < 1/4;
+     norm_a, norm_b  1/(sigma^2 S_aa), 1/(sigma^2 S_bb), >= 0;
+     F_out  device pointer to bin_hi - bin_lo + 1 floats;
+     cuda_stream  cudaStream_t or NULL.
+   The transforms' intermediate lives in a file-scope device array of
+   2 x 2^18 complex floats (4 MiB) and twiddle tables in another (about 20 KiB);
+   every GPU that loads the library holds them until the process exits.  On its
+   first call on a device (and on the first call for each transform length) the
+   entry point resolves the arrays' device addresses and fills the twiddle table
+   with a short kernel followed by a device synchronisation, so make that first
+   call before any stream capture.  Every call shares the arrays and nothing in
+   them has to start at zero (each call writes the whole intermediate it reads);
+   calls that overlap on the GPU (other streams, other host threads) race on them.
+   Synchronous with respect to the host.  Returns FSTAT_ERR_ARG for a NULL
+   pointer, a length beyond the maximum or any other invalid argument (nothing is
+   launched), FSTAT_ERR_CUDA if a CUDA call fails. */
+fstat_status fstat_cell_F_noalloc(const float *w, int64_t n, int64_t n_fft, double chirp_rate,
+                                  double norm_a, double norm_b, int64_t bin_lo, int64_t bin_hi,
+                                  float *F_out, void *cuda_stream);
+
 /* Release everything the plan holds.  NULL is accepted. */
 void fstat_plan_destroy(fstat_plan *plan);
 

@@ -79,6 +79,9 @@ _lib.fstat_plan_set_timing.argtypes = [_plan_p, i32]
 _lib.fstat_plan_set_timing.restype = i32
 _lib.fstat_plan_kernel_stats.argtypes = [_plan_p, P(fstat_kernel_stat), i32, P(i32)]
 _lib.fstat_plan_kernel_stats.restype = i32
+_lib.fstat_cell_F_noalloc.argtypes = [C.c_void_p, i64, i64, f64, f64, f64, i64, i64,
+                                       C.c_void_p, C.c_void_p]
+_lib.fstat_cell_F_noalloc.restype = i32
 _lib.fstat_plan_destroy.argtypes = [_plan_p]
 _lib.fstat_plan_destroy.restype = None
 _lib.fstat_status_string.argtypes = [i32]
@@ -88,7 +91,8 @@ _lib.fstat_plan_error.restype = C.c_char_p
 
 EXPORTED = ["fstat_plan_create", "fstat_search", "fstat_candidates_get", "fstat_debug_sky",
             "fstat_plan_get_info", "fstat_plan_set_timing", "fstat_plan_kernel_stats",
-            "fstat_plan_destroy", "fstat_status_string", "fstat_plan_error"]
+            "fstat_cell_F_noalloc", "fstat_plan_destroy", "fstat_status_string",
+            "fstat_plan_error"]
 
 
 def status_string(code: int) -> str:
@@ -258,6 +262,16 @@ class Plan:
 
     def __exit__(self, *a):
         self.close()
+
+
+def cell_F_noalloc(w_dev_ptr: int, n: int, n_fft: int, chirp_rate: float, norm_a: float,
+                   norm_b: float, bin_lo: int, bin_hi: int, F_out_dev_ptr: int,
+                   stream: Optional[int] = None) -> int:
+    """fstat_cell_F_noalloc through the C ABI (device pointers as integers);
+    returns the status code."""
+    return _lib.fstat_cell_F_noalloc(C.c_void_p(w_dev_ptr), int(n), int(n_fft), float(chirp_rate),
+                                     float(norm_a), float(norm_b), int(bin_lo), int(bin_hi),
+                                     C.c_void_p(F_out_dev_ptr), C.c_void_p(stream) if stream else None)
 
 
 def plan_create_status(desc_kwargs_bands, **kw) -> int:
