@@ -315,10 +315,13 @@ void create_impl(Plan &p, const fstat_plan_desc *d) {
     if (fp32) {
         // several worker streams, each running launch pairs of a batch of cells on its
         // own scratch slot: one stream's partial last wave overlaps the next grids
-        p.n_workers = 3;
+        // one stream with large launches is as fast as several overlapping streams
+        // and keeps the per-launch event timings free of overlap
+        p.n_workers = 1;
         if (const char *v = getenv("FSTAT_STREAMS")) p.n_workers = std::max(1, std::min(8, atoi(v)));
-        const int64_t budget = int64_t(128) << 20;   // per worker slot
+        const int64_t budget = int64_t(4) << 30;     // per worker slot
         p.cell_batch = std::max<int64_t>(1, std::min<int64_t>(4096, budget / (2 * max_nfft * (int64_t)tsz)));
+        p.cell_batch = std::min<int64_t>(p.cell_batch, p.sky_batch * d->n_spin);
         if (const char *v = getenv("FSTAT_CELL_BATCH")) p.cell_batch = std::max(1, std::min(65535, atoi(v)));
     } else {
         p.n_workers = 1;
