@@ -146,20 +146,22 @@ __global__ void __launch_bounds__(256) k_geometry(GeoArgs g) {
         // Keys cubic (a = -1/2) on the upsampled series, periodic indexing
         const double p = (double)g.U * u;
         const double pf = floor(p);
-        int64_t i0 = (int64_t)pf - 1;
-        i0 %= g.m_up;
-        if (i0 < 0) i0 += g.m_up;
+        // taps i0 .. i0 + 3 around floor(p), periodic: inside the window p lies in
+        // [0, U (n - 1)], so only i0 = -1 and indices >= U n wrap (a single step)
         int64_t idx[4];
+        if (valid) {
+            const int64_t i0 = (int64_t)pf - 1;
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            int64_t v = i0 + q;
-            idx[q] = v >= g.m_up ? v - g.m_up : v;
+            for (int q = 0; q < 4; ++q) {
+                const int64_t v = i0 + q;
+                idx[q] = v < 0 ? v + g.m_up : (v >= g.m_up ? v - g.m_up : v);
+            }
         }
         // band-offset phase, cycles, reduced in FP64
         const double cyc = __dmul_rn(g.f_off, d2);
         const double fr = __dsub_rn(cyc, floor(cyc));
         if constexpr (FP32) {
-            const float hr = (float)(h - kTwoPi * rint(h / kTwoPi));
+            const float hr = (float)(h - kTwoPi * rint(h * (1.0 / kTwoPi)));
             float s1, c1;
             sincosf(hr, &s1, &c1);
             const float c2 = c1 * c1 - s1 * s1, s2 = 2.f * s1 * c1;

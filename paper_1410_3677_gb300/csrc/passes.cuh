@@ -181,8 +181,11 @@ struct SearchLoadF64 {
 };
 
 // ------------------------------------------------------------------ pass 1 storer
-// Applies the inter-pass twiddle W_N^{k1 l2} = hi[m >> log N1] * lo[m & (N1-1)],
-// m = k1 l2 < N, and writes the transposed tile into scratch slot blockIdx.y.
+// Applies the inter-pass twiddle W_N^{k1 l2} and writes the transposed tile into
+// scratch slot blockIdx.y.  A job's outputs sit at l2 = j + r JPF, so its
+// twiddles are W^{k1 j} (W^{k1 JPF})^r: two table lookups per job, then complex
+// powers, instead of a scattered lookup per element.  A lookup of W_N^m, m < N,
+// is hi[m >> log N1] lo[m & (N1 - 1)].
 template <typename T, class C, int DIR>
 struct ScratchStore {
     using V = typename Vec2<T>::type;
@@ -198,22 +201,20 @@ struct ScratchStore {
         has_b = 2 * p + 1 < n_tr;
         k1_0 = blockIdx.x * C::F;
     }
+    __device__ __forceinline__ V wn(int m) const {
+        const V th = __ldg(reinterpret_cast<const V *>(hi) + (m >> C::LOGN1));
+        const V tl = __ldg(reinterpret_cast<const V *>(lo) + (m & (C::N1 - 1)));
+        return V{th.x * tl.x - th.y * tl.y, th.x * tl.y + th.y * tl.x};
+    }
     template <int R, int JPF>
     __device__ __forceinline__ void store(int f, int j, T *ra, T *ia, T *rb, T *ib) const {
-        using V = typename Vec2<T>::type;
         const int k1 = k1_0 + f;
-        V th[R], tl[R];
-#pragma unroll
-        for (int r = 0; r < R; ++r) {      // table loads first
-            const int m = k1 * (j + r * JPF);
-            th[r] = __ldg(reinterpret_cast<const V *>(hi) + (m >> C::LOGN1));
-            tl[r] = __ldg(reinterpret_cast<const V *>(lo) + (m & (C::N1 - 1)));
-        }
+        V w = wn(k1 * j);
+        const V st = wn(k1 * JPF);
 #pragma unroll
         for (int r = 0; r < R; ++r) {
             const int l2 = j + r * JPF;
-            T wr = th[r].x * tl[r].x - th[r].y * tl[r].y, wi = th[r].x * tl[r].y + th[r].y * tl[r].x;
-            if (DIR > 0) wi = -wi;
+            const T wr = w.x, wi = (DIR > 0) ? -w.y : w.y;
             T xr = ra[r], xi = ia[r];
             cmul_tw(xr, xi, wr, wi);
             base[(int64_t)l2 * C::N1 + k1] = V{xr, xi};
@@ -222,6 +223,7 @@ struct ScratchStore {
                 cmul_tw(xr, xi, wr, wi);
                 base[C::N + (int64_t)l2 * C::N1 + k1] = V{xr, xi};
             }
+            if (r + 1 < R) w = V{w.x * st.x - w.y * st.y, w.x * st.y + w.y * st.x};
         }
     }
 };
