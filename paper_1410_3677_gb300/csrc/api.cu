@@ -340,6 +340,7 @@ void create_impl(Plan &p, const fstat_plan_desc *d) {
         if (const char *v = getenv("FSTAT_TEST_WITHHOLD_ITEM")) p.withhold_item = atoll(v);
         if (const char *v = getenv("FSTAT_PERSISTENT")) p.use_persistent = atoi(v) != 0;
         if (const char *v = getenv("FSTAT_ELEMS_PER_THREAD")) p.elems_per_thread = atoi(v) == 8 ? 8 : 16;
+        if (const char *v = getenv("FSTAT_ENGINE")) p.engine = atoi(v) == 1 ? 1 : 2;
     }
     p.scratch = dalloc<unsigned char>(p, scratch_bytes, n_alloc);
     p.bw_elems = 2 * p.n_max + 2 * max_m;

@@ -1,0 +1,229 @@
+// Second FFT engine: one transform per thread group, 32 complex elements per
+// thread, and every pass length M <= 1024 split into at most two register
+// stages (M = R0 R1 with R0, R1 <= 32), so the data crosses shared memory once
+// per pass instead of twice.
+//
+// A CTA transforms SEQ independent length-M sequences (for the F-statistic the
+// F_a and F_b sequences of F tiles: s = t F + f, t = 0 for a, 1 for b).  Stage 0
+// is a radix-R0 DFT of the elements j + r M/R0 of one sequence; stage 1 twiddles
+// by W_M^{r j} and takes radix-R1 DFTs; outputs land at j + r R0.  Shared memory
+// holds complex elements (float2) in rows of LD elements with element i at
+// i + i/32, which makes both scatter and gather of the two-stage plan free of
+// bank conflicts for M = 512 and leaves every radix offset an immediate.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "fft_engine.cuh"
+
+namespace fstat {
+namespace eng2 {
+
+using eng::Vec2T;
+
+// ------------------------------------------------------------------ constants
+// e^{-2 pi i k/32} from the first-octant values cos(pi m/16), sin(pi m/16).
+__host__ __device__ constexpr double oct_cos(int m) {
+    return m == 0 ? 1.0 : m == 1 ? 0.98078528040323044913 : m == 2 ? 0.92387953251128675613
+         : m == 3 ? 0.83146961230254523708 : m == 4 ? 0.70710678118654752440
+         : m == 5 ? 0.55557023301960222474 : m == 6 ? 0.38268343236508977173
+         : m == 7 ? 0.19509032201612826785 : 0.0;
+}
+__host__ __device__ constexpr double oct_sin(int m) { return oct_cos(8 - m); }
+__host__ __device__ constexpr double w32_re(int k) {
+    return (k / 8) % 4 == 0 ? oct_cos(k % 8) : (k / 8) % 4 == 1 ? -oct_sin(k % 8)
+         : (k / 8) % 4 == 2 ? -oct_cos(k % 8) : oct_sin(k % 8);
+}
+__host__ __device__ constexpr double w32_im(int k) {   // -sin(2 pi k / 32)
+    return (k / 8) % 4 == 0 ? -oct_sin(k % 8) : (k / 8) % 4 == 1 ? -oct_cos(k % 8)
+         : (k / 8) % 4 == 2 ? oct_sin(k % 8) : oct_cos(k % 8);
+}
+
+// ------------------------------------------------------------------ register DFTs
+// Natural order in and out; DIR = -1 is the forward transform.
+template <int R, int DIR, typename T>
+__device__ __forceinline__ void dft(T *re, T *im);
+
+// Radix-4 decimation in time: 4 sub-DFTs of length R/4 over x[4m + q], then for
+// each k < R/4 the twiddles W_R^{q k} and a 4-point DFT across q.
+template <int R, int DIR, typename T>
+__device__ __forceinline__ void dft_r4(T *re, T *im) {
+    constexpr int n = R / 4;
+    T sr[4][n], si[4][n];
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+        for (int m = 0; m < n; ++m) { sr[q][m] = re[4 * m + q]; si[q][m] = im[4 * m + q]; }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) dft<n, DIR>(sr[q], si[q]);
+#pragma unroll
+    for (int k = 0; k < n; ++k) {
+        T zr[4], zi[4];
+        zr[0] = sr[0][k]; zi[0] = si[0][k];
+#pragma unroll
+        for (int q = 1; q < 4; ++q) {
+            const int e = (32 / R) * q * k;   // W_R^{q k} = W_32^{(32/R) q k}
+            const T wr = (T)w32_re(e);
+            const T wi = DIR < 0 ? (T)w32_im(e) : -(T)w32_im(e);
+            zr[q] = sr[q][k] * wr - si[q][k] * wi;
+            zi[q] = sr[q][k] * wi + si[q][k] * wr;
+        }
+        eng::dft4<DIR>(zr[0], zi[0], zr[1], zi[1], zr[2], zi[2], zr[3], zi[3]);
+#pragma unroll
+        for (int p = 0; p < 4; ++p) { re[k + n * p] = zr[p]; im[k + n * p] = zi[p]; }
+    }
+}
+
+template <int R, int DIR, typename T>
+__device__ __forceinline__ void dft(T *re, T *im) {
+    if constexpr (R == 32 || R == 16) dft_r4<R, DIR>(re, im);
+    else eng::dft<R, DIR>(re, im);
+}
+
+// ------------------------------------------------------------------ plan
+__host__ __device__ constexpr int radix0(int M) { return M <= 32 ? M : (M >= 512 ? 32 : (M >= 128 ? 16 : 8)); }
+__host__ __device__ constexpr int radix1(int M) { return M <= 32 ? 1 : M / radix0(M); }
+__host__ __device__ constexpr int pad(int i) { return i + (i >> 5); }
+__host__ __device__ constexpr int row_ld(int M) { return (pad(M - 1) + 1) | 1; }
+// stage-1 twiddles: rows b < log2 R1 of W_M^{2^b j}, j < R0
+__host__ __device__ constexpr int ilog2c(int x) { return x <= 1 ? 0 : 1 + ilog2c(x >> 1); }
+__host__ __device__ constexpr int tw_entries(int M) { return M <= 32 ? 1 : ilog2c(radix1(M)) * radix0(M); }
+
+template <typename T, int M, int SEQ>
+__host__ __device__ constexpr size_t exch_bytes() { return 2 * sizeof(T) * (size_t)SEQ * row_ld(M); }
+template <typename T, int M, int SEQ>
+__host__ __device__ constexpr size_t smem_bytes() {
+    return exch_bytes<T, M, SEQ>() + 2 * sizeof(T) * (size_t)tw_entries(M);
+}
+
+// Mappings of a thread's i-th job of a stage to (sequence s, butterfly j) and of
+// s to (transform t, tile column or row f):
+//   kMapFJ  consecutive threads take consecutive sequences, s = 2 f + t (the a
+//           and b halves of one float4 input side by side: coalesced access to a
+//           strided tile of columns), CTA-wide barriers;
+//   kMapW   s = t SEQ/2 + f; a warp holds F_a and F_b of the same tile rows in
+//           its two halves (lanes l and l ^ 16 share j and f), warp-level
+//           synchronisation only.
+constexpr int kMapFJ = 1, kMapW = 2;
+
+struct Job {
+    int s, t, f, j;
+};
+
+template <int MAPM, int SEQ, int TPF, int THREADS>
+__device__ __forceinline__ Job job(int i) {
+    Job q;
+    if constexpr (MAPM == kMapW) {
+        constexpr int G = 32 / TPF;          // groups per warp, G/2 tile rows
+        const int w = (int)threadIdx.x >> 5, l = (int)threadIdx.x & 31;
+        const int gi = l / TPF;
+        q.t = gi < G / 2 ? 0 : 1;
+        q.f = w * (G / 2) + (gi % (G / 2));
+        q.s = q.t * (SEQ / 2) + q.f;
+        q.j = l % TPF + TPF * i;
+    } else {
+        const int x = (int)threadIdx.x + i * THREADS;
+        q.s = x % SEQ;
+        q.j = x / SEQ;
+        q.t = q.s & 1;
+        q.f = q.s >> 1;
+    }
+    return q;
+}
+
+// Fills the stage-1 twiddle table, entry b R0 + j = W_M^{2^b j}, from the forward
+// table tw[m] = e^{-2 pi i m / M}.
+template <typename T, int M, int THREADS>
+__device__ __forceinline__ void fill_twiddles(typename Vec2T<T>::type *tws, const T *__restrict__ tw) {
+    if constexpr (M > 32) {
+        constexpr int R0 = radix0(M), n = tw_entries(M);
+        for (int e = (int)threadIdx.x; e < n; e += THREADS) {
+            const int m = (e % R0) << (e / R0);
+            tws[e] = typename Vec2T<T>::type{tw[2 * m], tw[2 * m + 1]};
+        }
+    }
+}
+
+// One pass over a tile.  LD::load<R0, M/R0>(job, re, im) yields the elements
+// j + r M/R0 of sequence (t, f); ST::store<R, JPF>(job, re, im) receives outputs
+// j + r JPF (R = R1, JPF = R0 after two stages; R = M, JPF = 1 after one).
+template <typename T, int M, int SEQ, int EH, int DIR, int MAPM, class LD, class ST>
+__device__ __forceinline__ void run_pass(LD &ld, ST &st, const T *__restrict__ tw) {
+    using V = typename Vec2T<T>::type;
+    constexpr int R0 = radix0(M), R1 = radix1(M);
+    constexpr int TPF = M / EH;
+    constexpr int THREADS = SEQ * TPF;
+    constexpr int RL = row_ld(M);
+    constexpr int JPF0 = M / R0, NJ0 = EH / R0;
+    static_assert(EH % R0 == 0 && (R1 == 1 || EH % R1 == 0), "elements per thread vs radix");
+    static_assert(MAPM != kMapW || (TPF <= 16 && 32 % TPF == 0), "warp mapping needs <= 16 threads per sequence");
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    V *sd = reinterpret_cast<V *>(smem_raw);
+    V *tws = reinterpret_cast<V *>(smem_raw + exch_bytes<T, M, SEQ>());
+    fill_twiddles<T, M, THREADS>(tws, tw);
+    if constexpr (R1 > 1) __syncthreads();
+
+    T re[EH], im[EH];
+#pragma unroll
+    for (int i = 0; i < NJ0; ++i) ld.template load<R0, JPF0>(job<MAPM, SEQ, TPF, THREADS>(i), &re[i * R0], &im[i * R0]);
+#pragma unroll
+    for (int i = 0; i < NJ0; ++i) dft<R0, DIR>(&re[i * R0], &im[i * R0]);
+    if constexpr (R1 == 1) {
+#pragma unroll
+        for (int i = 0; i < NJ0; ++i) st.template store<R0, JPF0>(job<MAPM, SEQ, TPF, THREADS>(i), &re[i * R0], &im[i * R0]);
+    } else {
+        // scatter: stage-0 output r of butterfly j goes to j R0 + r
+#pragma unroll
+        for (int i = 0; i < NJ0; ++i) {
+            const Job q = job<MAPM, SEQ, TPF, THREADS>(i);
+            V *p = sd + q.s * RL + pad(q.j * R0);
+#pragma unroll
+            for (int r = 0; r < R0; ++r) p[pad(r)] = V{re[i * R0 + r], im[i * R0 + r]};
+        }
+        if constexpr (MAPM == kMapW) __syncwarp(); else __syncthreads();
+        constexpr int NJ1 = EH / R1;
+        constexpr int LR1 = ilog2c(R1);
+#pragma unroll
+        for (int i = 0; i < NJ1; ++i) {
+            const Job q = job<MAPM, SEQ, TPF, THREADS>(i);   // q.j < R0
+            const V *p = sd + q.s * RL + pad(q.j);
+            T *xr = &re[i * R1], *xi = &im[i * R1];
+#pragma unroll
+            for (int r = 0; r < R1; ++r) {
+                const V v = p[pad(r * R0)];
+                xr[r] = v.x; xi[r] = v.y;
+            }
+            // W_M^{r j}: powers of two from the table, the rest as products
+            // W^{r j} = W^{h j} W^{(r - h) j}, h the top bit of r (<= LR1 - 1 products deep)
+            T wr[R1], wi[R1];
+#pragma unroll
+            for (int b = 0; b < LR1; ++b) {
+                const V w = tws[b * R0 + q.j];
+                wr[1 << b] = w.x;
+                wi[1 << b] = DIR < 0 ? w.y : -w.y;
+            }
+#pragma unroll
+            for (int r = 3; r < R1; ++r) {
+                int h = r;   // top bit of r (folds to a constant once unrolled)
+                h |= h >> 1; h |= h >> 2; h |= h >> 4;
+                h = (h + 1) >> 1;
+                if (h != r) {
+                    wr[r] = wr[h] * wr[r - h] - wi[h] * wi[r - h];
+                    wi[r] = wr[h] * wi[r - h] + wi[h] * wr[r - h];
+                }
+            }
+#pragma unroll
+            for (int r = 1; r < R1; ++r) {
+                const T a = xr[r] * wr[r] - xi[r] * wi[r], b = xr[r] * wi[r] + xi[r] * wr[r];
+                xr[r] = a; xi[r] = b;
+            }
+            dft<R1, DIR>(xr, xi);
+        }
+#pragma unroll
+        for (int i = 0; i < NJ1; ++i) st.template store<R1, R0>(job<MAPM, SEQ, TPF, THREADS>(i), &re[i * R1], &im[i * R1]);
+    }
+}
+
+}  // namespace eng2
+}  // namespace fstat

@@ -107,6 +107,7 @@ struct Plan {
     std::vector<cudaEvent_t> ev_done[2];
     std::vector<cudaEvent_t> ev_join;
     int elems_per_thread = 16;     // FP32 batched passes: 16 or 8 complex elements per thread
+    int engine = 2;                // FP32 batched passes, 2^12 .. 2^19: 2 = two-stage engine, 1 = radix-8 engine
 
     // Bluestein / generic-FFT work buffers (double2)
     double *bw = nullptr;

@@ -180,9 +180,12 @@ def test_uneven_bands_float32_band_offsets(fs, form):
 
 # ------------------------------------------------------------------ edge cases
 @pytest.mark.parametrize("form", [0, 1])
-@pytest.mark.parametrize("n,n_fft,U", [(100, 256, 2), (129, 0, 1), (1000, 8192, 4), (4096, 8192, 3)])
+@pytest.mark.parametrize("n,n_fft,U", [(100, 256, 2), (129, 0, 1), (1000, 8192, 4), (4096, 8192, 3),
+                                         (2000, 1 << 12, 2), (7000, 1 << 14, 2), (30000, 1 << 16, 2),
+                                         (200000, 1 << 19, 2)])
 def test_small_and_odd_shapes(fs, form, n, n_fft, U):
-    """Smallest transform, odd length, explicit longer n_fft, U = 1, 3, 4."""
+    """Smallest transform, odd length, explicit longer n_fft, U = 1, 3, 4, and
+    transform lengths 2^12 .. 2^19 beyond the standard workloads."""
     w0 = S.workload(1, n_sky=4, n_spin=2)
     b = S.make_band(n, 2.0, 77 + n, 1.0, w0.alpha, w0.delta, w0.fdot, [], n_fft=n_fft)
     w = S.Workload("small", [b], w0.alpha, w0.delta, w0.fdot, 10.0, upsample=U)

@@ -41,22 +41,52 @@ def _run(fs, w, thr, env=None, **kw):
     return p, rc, c, total
 
 
-@pytest.mark.parametrize("env", [{"FSTAT_PERSISTENT": "1", "FSTAT_PERSIST_BATCH": "1", "FSTAT_PERSIST_SLOTS": "2"},
-                                 {"FSTAT_PERSISTENT": "1", "FSTAT_PERSIST_BATCH": "3", "FSTAT_PERSIST_SLOTS": "3"},
-                                 {"FSTAT_PERSISTENT": "1", "FSTAT_PERSIST_BATCH": "5", "FSTAT_PERSIST_SLOTS": "8"},
-                                 {"FSTAT_ELEMS_PER_THREAD": "8"},
-                                 {"FSTAT_ELEMS_PER_THREAD": "8", "FSTAT_CELL_BATCH": "7", "FSTAT_STREAMS": "2"}])
-def test_launch_shapes_match_bitwise(fs, env):
+R8 = {"FSTAT_PERSISTENT": "0", "FSTAT_ENGINE": "1"}     # radix-8 engine, two launches per batch
+TWO = {"FSTAT_PERSISTENT": "0"}                           # default: two-stage engine
+
+
+@pytest.mark.parametrize("base,env", [
+    (R8, {"FSTAT_PERSISTENT": "1", "FSTAT_PERSIST_BATCH": "1", "FSTAT_PERSIST_SLOTS": "2"}),
+    (R8, {"FSTAT_PERSISTENT": "1", "FSTAT_PERSIST_BATCH": "3", "FSTAT_PERSIST_SLOTS": "3"}),
+    (R8, {"FSTAT_PERSISTENT": "1", "FSTAT_PERSIST_BATCH": "5", "FSTAT_PERSIST_SLOTS": "8"}),
+    (R8, {"FSTAT_ENGINE": "1", "FSTAT_ELEMS_PER_THREAD": "8"}),
+    (R8, {"FSTAT_ENGINE": "1", "FSTAT_ELEMS_PER_THREAD": "8", "FSTAT_CELL_BATCH": "7", "FSTAT_STREAMS": "2"}),
+    (TWO, {"FSTAT_CELL_BATCH": "7", "FSTAT_STREAMS": "2"}),
+    (TWO, {"FSTAT_CELL_BATCH": "1", "FSTAT_STREAMS": "3"}),
+])
+def test_launch_shapes_match_bitwise(fs, base, env):
     """The queue-fed persistent kernel and other tile / batch shapes against the
-    default two-launches-per-batch form.  Tiny workload (N_fft = 2^13) and a two-sidereal-day band (2^18) with cell
-    counts that leave a partial last batch."""
+    two-launches-per-batch form of the same FFT engine.  Tiny workload (N_fft =
+    2^13) and a two-sidereal-day band (2^18) with cell counts that leave a partial
+    last batch."""
     for w in (S.workload(1, n_sky=9, n_spin=3), S.workload(3, n_sky=5, n_spin=3)):
-        p0, rc0, ref, t0 = _run(fs, w, 8.0, {"FSTAT_PERSISTENT": "0"})
+        p0, rc0, ref, t0 = _run(fs, w, 8.0, base)
         p0.close()
         p1, rc1, got, t1 = _run(fs, w, 8.0, env)
         p1.close()
         assert rc0 == rc1 == fs.FSTAT_OK
         assert t0 == t1 and np.array_equal(ref, got)
+
+
+@pytest.mark.parametrize("n,n_fft", [(2000, 1 << 12), (4096, 1 << 13), (7000, 1 << 14), (16000, 1 << 15),
+                                     (30000, 1 << 16), (60000, 1 << 17), (86164, 1 << 18), (200000, 1 << 19)])
+def test_engines_agree_on_every_bin(fs, n, n_fft):
+    """The two-stage and the radix-8 FFT engines, every bin of every cell, at each
+    transform length the two-stage engine serves: each is within 1e-4 max(F, 2)
+    of the oracle, so they agree within twice that."""
+    w0 = S.workload(1, n_sky=3, n_spin=2)
+    b = S.make_band(n, 2.0, 5 + n, 1.0, w0.alpha, w0.delta, w0.fdot, [], n_fft=n_fft)
+    w = S.Workload("engines", [b], w0.alpha, w0.delta, w0.fdot, 10.0, upsample=2)
+    out = []
+    for env in (R8, TWO):
+        p, rc, c, total = _run(fs, w, -1.0, env)
+        p.close()
+        assert rc == fs.FSTAT_OK and total == 6 * (n_fft // 2 - 1)
+        out.append(c)
+    a, b = out
+    for key in ("band", "sky", "spin", "bin"):
+        assert np.array_equal(a[key], b[key])
+    assert np.all(np.abs(a["F"] - b["F"]) <= 2e-4 * np.maximum(np.maximum(a["F"], b["F"]), 2.0))
 
 
 def test_queue_cell_ranges(fs):
