@@ -141,8 +141,9 @@ struct ScratchLoad2 {
 // atomic per warp and output slot.  Lanes l (F_a) and l ^ 16 (F_b) hold the same
 // bins; each forms |.|^2 of its own values and trades half of them with its
 // partner, so the a lane evaluates F on the first half of the outputs and the b
-// lane on the second.
-template <class C>
+// lane on the second.  LOWER: the bin range lies below N/2, so only the outputs
+// l1 < N1/2 (r < R/2) are used and the rest of the last DFT is never computed.
+template <class C, bool LOWER>
 struct SearchEpi2 {
     const double *norm;      // [sky_local][2]
     int n_spin;
@@ -153,7 +154,7 @@ struct SearchEpi2 {
     CandRecord *out;
     unsigned long long *count;
     unsigned long long cap;
-    float na, nb;
+    float na, nb, thr_half;
     uint32_t cell;
     int l2_0;
     __device__ void init() {
@@ -163,26 +164,28 @@ struct SearchEpi2 {
         nb = (float)norm[2 * (sky - s0) + 1];
         cell = cell_base + (uint32_t)c;
         l2_0 = blockIdx.x * C::F;
+        thr_half = 0.5f * thr;   // 2F > thr  <=>  F > thr / 2, both sides exact
     }
     template <int R, int JPF>
     __device__ __forceinline__ void store(const eng2::Job &q, float *re, float *im) const {
-        constexpr int H = R / 2;
+        constexpr int H = (LOWER ? R / 2 : R) / 2;   // values per lane
         const int lane = threadIdx.x & 31;
-        float pw[R];
-#pragma unroll
-        for (int r = 0; r < R; ++r) pw[r] = re[r] * re[r] + im[r] * im[r];
         float Fv[H];
-        int64_t bin[H];
-        bool any = false;
         bool pr[H];
+        bool any = false;
+        // bins < 2^19: 32-bit arithmetic; lo <= bin <= hi as one unsigned compare
+        const int bin0 = C::N2 * (q.j + q.t * H * JPF) + l2_0 + q.f;
+        const int lo = (int)bin_lo;
+        const unsigned span = (unsigned)(bin_hi - bin_lo);
 #pragma unroll
         for (int r = 0; r < H; ++r) {
-            const float mine = q.t == 0 ? pw[r] : pw[r + H];
-            const float send = q.t == 0 ? pw[r + H] : pw[r];
-            const float other = __shfl_xor_sync(0xffffffffu, send, 16);
-            Fv[r] = q.t == 0 ? mine * na + other * nb : other * na + mine * nb;
-            bin[r] = (int64_t)C::N2 * (q.j + (r + q.t * H) * JPF) + (l2_0 + q.f);
-            pr[r] = (bin[r] >= bin_lo) && (bin[r] <= bin_hi) && (2.f * Fv[r] > thr);
+            // this lane's |x|^2 at outputs r (a lane's bins) and r + H (b lane's)
+            const float p_lo = re[r] * re[r] + im[r] * im[r];
+            const float p_hi = re[r + H] * re[r + H] + im[r + H] * im[r + H];
+            const float other = __shfl_xor_sync(0xffffffffu, q.t == 0 ? p_hi : p_lo, 16);
+            Fv[r] = q.t == 0 ? p_lo * na + other * nb : other * na + p_hi * nb;
+            const unsigned off = (unsigned)(bin0 + r * C::N2 * JPF - lo);
+            pr[r] = (off <= span) && (Fv[r] > thr_half);
             any |= pr[r];
         }
         if (!__any_sync(0xffffffffu, any)) return;
@@ -196,15 +199,17 @@ struct SearchEpi2 {
                 b0 = __shfl_sync(0xffffffffu, b0, leader);
                 if (pr[r]) {
                     const unsigned long long idx = b0 + __popc(m & ((1u << lane) - 1u));
-                    if (idx < cap) out[idx] = CandRecord{cell, (uint32_t)bin[r], (double)Fv[r]};
+                    if (idx < cap) out[idx] = CandRecord{cell, (uint32_t)(bin0 + r * C::N2 * JPF), (double)Fv[r]};
                 }
             }
         }
     }
 };
 
+// Pass 2 holds fewer live values (no demodulation, no twiddle powers) and fits
+// three CTAs per SM (<= 85 registers, 3 x 68 KB of shared memory); pass 1 two.
 template <int LOGN, int PASS, int MAPM, class LD, class ST>
-__global__ void __launch_bounds__(256, 2) k_pass2(LD ld, ST st, const float *__restrict__ tw) {
+__global__ void __launch_bounds__(256, PASS == 2 ? 3 : 2) k_pass2(LD ld, ST st, const float *__restrict__ tw) {
     using C = Cfg2<LOGN, PASS>;
     ld.init();
     st.init();

@@ -7,6 +7,29 @@
 namespace fstat {
 namespace {
 
+template <int LOGN, bool LOWER>
+void launch_pass2(const Plan &p, int band_idx, const BandDev &b, int64_t s0, int64_t c0, int64_t nc,
+                  cudaStream_t s, const CellBufs &cb, const ScratchLoad2<Cfg2<LOGN, 2>> &ld2,
+                  const float *tw_in1) {
+    using C2 = Cfg2<LOGN, 2>;
+    SearchEpi2<C2, LOWER> st2{};
+    st2.norm = cb.norm;
+    st2.n_spin = (int)p.desc.n_spin;
+    st2.c0 = c0;
+    st2.s0 = s0;
+    st2.cell_base = (uint32_t)((int64_t)band_idx * p.desc.n_sky * p.desc.n_spin);
+    st2.bin_lo = b.lo;
+    st2.bin_hi = b.hi;
+    st2.thr = (float)p.desc.thr_2F;
+    st2.out = p.cand;
+    st2.count = p.cand_count;
+    st2.cap = (unsigned long long)p.cand_capacity;
+    auto k2 = k_pass2<LOGN, 2, eng2::kMapW, ScratchLoad2<C2>, SearchEpi2<C2, LOWER>>;
+    static bool attr2 = false;
+    if (!attr2) { set_smem(k2, C2::SMEM); attr2 = true; }
+    k2<<<dim3(C2::TILES, (unsigned)nc), C2::THREADS, C2::SMEM, s>>>(ld2, st2, tw_in1);
+}
+
 template <int LOGN>
 int launch_search2(const Plan &p, int band_idx, const BandDev &b, int64_t s0, int64_t c0,
                    int64_t nc, cudaStream_t s, cudaEvent_t mid, const CellBufs &cb) {
@@ -35,22 +58,8 @@ int launch_search2(const Plan &p, int band_idx, const BandDev &b, int64_t s0, in
 
     ScratchLoad2<C2> ld2{};
     ld2.scratch = reinterpret_cast<const float2 *>(cb.scratch);
-    SearchEpi2<C2> st2{};
-    st2.norm = cb.norm;
-    st2.n_spin = n_spin;
-    st2.c0 = c0;
-    st2.s0 = s0;
-    st2.cell_base = (uint32_t)((int64_t)band_idx * p.desc.n_sky * p.desc.n_spin);
-    st2.bin_lo = b.lo;
-    st2.bin_hi = b.hi;
-    st2.thr = (float)p.desc.thr_2F;
-    st2.out = p.cand;
-    st2.count = p.cand_count;
-    st2.cap = (unsigned long long)p.cand_capacity;
-    auto k2 = k_pass2<LOGN, 2, eng2::kMapW, ScratchLoad2<C2>, SearchEpi2<C2>>;
-    static bool attr2 = false;
-    if (!attr2) { set_smem(k2, C2::SMEM); attr2 = true; }
-    k2<<<dim3(C2::TILES, (unsigned)nc), C2::THREADS, C2::SMEM, s>>>(ld2, st2, tw->in1_f);
+    if (b.hi < (int64_t)C2::N / 2) launch_pass2<LOGN, true>(p, band_idx, b, s0, c0, nc, s, cb, ld2, tw->in1_f);
+    else launch_pass2<LOGN, false>(p, band_idx, b, s0, c0, nc, s, cb, ld2, tw->in1_f);
     return 2;
 }
 
