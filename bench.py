@@ -210,18 +210,24 @@ def run_reference(args, rank, world):
 
 
 # ----------------------------------------------------------------------------- our arm
-def traffic_record(kernel_name):
+# Files that define the FFT/F-statistic kernels (host orchestration excluded): a
+# change to any of them voids the recorded DRAM traffic.
+KERNEL_SOURCES = ("fft_engine.cuh", "fft_engine2.cuh", "passes.cuh", "passes2.cuh",
+                  "search_launch.cuh", "search_f32.cu", "search_f64.cu", "geometry.cu",
+                  "search_persistent.cu", "sync_ptx.cuh", "fstat_internal.h")
+
+
+def traffic_record(kernel_name, flops_per_launch):
     """DRAM bytes per launch from the committed ncu summary, if it was taken on the
-    current kernel source (else None)."""
+    current kernel source and on launches of the same size (else None)."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as fh:
             rec = json.load(fh)
     except OSError:
         return None
-    src = source_hash()
     k = rec.get(kernel_name)
-    if not k or k.get("source_hash") != src:
+    if not k or k.get("source_hash") != source_hash() or k.get("flops_per_launch") != flops_per_launch:
         return None
     return k.get("dram_bytes_per_launch")
 
@@ -229,7 +235,7 @@ def traffic_record(kernel_name):
 def source_hash():
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1410_3677_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
+    for f in KERNEL_SOURCES:
         with open(os.path.join(csrc, f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -298,7 +304,7 @@ def run_ours(args, rank, world, dist):
               if v["timed_launches"] else None for k, v in kstats.items()}
     roofline = {"bound": "alu", "kernel": dname, "achieved": round(achieved, 3),
                 "peak": round(peak, 2), "unit": "TFLOP/s", "frac": round(achieved / peak, 4),
-                "traffic": traffic_record(dname),
+                "traffic": traffic_record(dname, dv["flops_per_launch"]),
                 "peak_basis": f"{SMS} SMs x {FP32_LANES} FP32 lanes x 2 flop/FMA x {sm_max:.0f} MHz (max SM clock)",
                 "flops_per_launch": dv["flops_per_launch"], "avg_launch_ms": round(avg_ms, 5),
                 "timed_launches": dv["timed_launches"], "kernel_time_share": shares}

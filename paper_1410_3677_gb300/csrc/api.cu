@@ -6,7 +6,10 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
+#include <memory>
 #include <new>
+#include <thread>
 #include <string>
 #include <vector>
 
@@ -609,6 +612,77 @@ fstat_status guarded(fstat_plan *p, F &&f) {
 
 using namespace fstat;
 
+namespace {
+
+inline uint64_t cand_key(const fstat::CandRecord &r) { return ((uint64_t)r.cell << 32) | r.bin; }
+
+// Runs f(t) for t in [0, nt) on nt threads (the calling thread takes t = 0).
+template <class Fn>
+void parallel_for_threads(int nt, Fn f) {
+    std::vector<std::thread> th;
+    for (int t = 1; t < nt; ++t) th.emplace_back(f, t);
+    f(0);
+    for (auto &x : th) x.join();
+}
+
+// Sorts the records by (cell, bin): a bucket pass over the cell range, then the
+// buckets sorted side by side.  rec and tmp hold n records; the result is in
+// the returned pointer (one of the two).
+fstat::CandRecord *sort_records(fstat::CandRecord *rec, fstat::CandRecord *tmp, int64_t n) {
+    using fstat::CandRecord;
+    auto less = [](const CandRecord &a, const CandRecord &b) { return cand_key(a) < cand_key(b); };
+    const unsigned hc = std::max(1u, std::thread::hardware_concurrency());
+    const int nt = (int)std::min<int64_t>(std::min(hc, 64u), std::max<int64_t>(1, n >> 16));
+    if (nt <= 1) {
+        std::sort(rec, rec + n, less);
+        return rec;
+    }
+    const int nb = 8 * nt;   // buckets
+    std::vector<uint32_t> lo_t(nt, UINT32_MAX), hi_t(nt, 0);
+    auto chunk = [&](int t, int64_t &a, int64_t &b) { a = n * t / nt; b = n * (t + 1) / nt; };
+    parallel_for_threads(nt, [&](int t) {
+        int64_t a, b;
+        chunk(t, a, b);
+        for (int64_t i = a; i < b; ++i) {
+            lo_t[t] = std::min(lo_t[t], rec[i].cell);
+            hi_t[t] = std::max(hi_t[t], rec[i].cell);
+        }
+    });
+    const uint64_t lo = *std::min_element(lo_t.begin(), lo_t.end());
+    const uint64_t span = *std::max_element(hi_t.begin(), hi_t.end()) - lo + 1;
+    auto bucket = [&](const CandRecord &r) { return (int)((r.cell - lo) * (uint64_t)nb / span); };
+    std::vector<int64_t> hist((size_t)nt * nb, 0);
+    parallel_for_threads(nt, [&](int t) {
+        int64_t a, b;
+        chunk(t, a, b);
+        int64_t *h = &hist[(size_t)t * nb];
+        for (int64_t i = a; i < b; ++i) ++h[bucket(rec[i])];
+    });
+    std::vector<int64_t> start(nb + 1, 0), off((size_t)nt * nb);
+    int64_t acc = 0;
+    for (int k = 0; k < nb; ++k) {
+        start[k] = acc;
+        for (int t = 0; t < nt; ++t) {
+            off[(size_t)t * nb + k] = acc;
+            acc += hist[(size_t)t * nb + k];
+        }
+    }
+    start[nb] = acc;
+    parallel_for_threads(nt, [&](int t) {
+        int64_t a, b;
+        chunk(t, a, b);
+        int64_t *o = &off[(size_t)t * nb];
+        for (int64_t i = a; i < b; ++i) tmp[o[bucket(rec[i])]++] = rec[i];
+    });
+    std::atomic<int> next{0};
+    parallel_for_threads(nt, [&](int) {
+        for (int k; (k = next.fetch_add(1)) < nb;) std::sort(tmp + start[k], tmp + start[k + 1], less);
+    });
+    return tmp;
+}
+
+}  // namespace
+
 extern "C" {
 
 fstat_status fstat_plan_create(fstat_plan **out, const fstat_plan_desc *desc) {
@@ -666,35 +740,39 @@ fstat_status fstat_candidates_get(fstat_plan *p, fstat_candidate *buf, int64_t c
         if (n_written) *n_written = 0;
         if (n_total) *n_total = 0;
         if (!p->searched) return FSTAT_OK;
+        if (n_total) *n_total = p->last_total;
+        if (cap == 0) return p->last_total > 0 ? FSTAT_ERR_OVERFLOW : FSTAT_OK;   // count only
         const int64_t kept = std::min<int64_t>(p->last_total, p->cand_capacity);
-        std::vector<CandRecord> rec((size_t)kept);
+        std::unique_ptr<CandRecord[]> rec(new CandRecord[(size_t)std::max<int64_t>(kept, 1)]);
+        std::unique_ptr<CandRecord[]> tmp(new CandRecord[(size_t)std::max<int64_t>(kept, 1)]);
         if (kept > 0)
-            check(cudaMemcpy(rec.data(), p->cand, kept * sizeof(CandRecord), cudaMemcpyDeviceToHost), "candidates");
-        std::sort(rec.begin(), rec.end(), [](const CandRecord &a, const CandRecord &b) {
-            return a.cell != b.cell ? a.cell < b.cell : a.bin < b.bin;
-        });
+            check(cudaMemcpy(rec.get(), p->cand, kept * sizeof(CandRecord), cudaMemcpyDeviceToHost), "candidates");
+        const CandRecord *sorted = sort_records(rec.get(), tmp.get(), kept);
         const int64_t nw = std::min<int64_t>(kept, cap);
         const fstat_plan_desc &d = p->desc;
-        for (int64_t i = 0; i < nw; ++i) {
-            const CandRecord &r = rec[(size_t)i];
-            const int64_t per_band = d.n_sky * d.n_spin;
-            const int band = (int)(r.cell / per_band);
-            const int64_t rem = r.cell - (int64_t)band * per_band;
-            fstat_candidate &c = buf[i];
-            c.band = band;
-            c.reserved = 0;
-            c.sky = rem / d.n_spin;
-            c.spin = rem % d.n_spin;
-            c.bin = r.bin;
-            c.alpha = p->h_alpha[(size_t)c.sky];
-            c.delta = p->h_delta[(size_t)c.sky];
-            c.fdot = p->h_fdot[(size_t)c.spin];
-            const BandDev &b = p->bands[(size_t)band];
-            c.freq = b.f_off + (double)r.bin / ((double)b.n_fft * b.dt);
-            c.F = r.F;
-        }
+        const int64_t per_band = d.n_sky * d.n_spin;
+        const unsigned hc = std::max(1u, std::thread::hardware_concurrency());
+        const int nt = (int)std::min<int64_t>(std::min(hc, 64u), std::max<int64_t>(1, nw >> 16));
+        parallel_for_threads(nt, [&](int t) {
+            for (int64_t i = nw * t / nt; i < nw * (t + 1) / nt; ++i) {
+                const CandRecord &r = sorted[i];
+                const int band = (int)(r.cell / per_band);
+                const int64_t rem = r.cell - (int64_t)band * per_band;
+                fstat_candidate &c = buf[i];
+                c.band = band;
+                c.reserved = 0;
+                c.sky = rem / d.n_spin;
+                c.spin = rem % d.n_spin;
+                c.bin = r.bin;
+                c.alpha = p->h_alpha[(size_t)c.sky];
+                c.delta = p->h_delta[(size_t)c.sky];
+                c.fdot = p->h_fdot[(size_t)c.spin];
+                const BandDev &b = p->bands[(size_t)band];
+                c.freq = b.f_off + (double)r.bin / ((double)b.n_fft * b.dt);
+                c.F = r.F;
+            }
+        });
         if (n_written) *n_written = nw;
-        if (n_total) *n_total = p->last_total;
         return p->last_total > nw ? FSTAT_ERR_OVERFLOW : FSTAT_OK;
     });
 }

@@ -197,12 +197,12 @@ class Plan:
         if cap is None:
             _lib.fstat_candidates_get(self._h, None, 0, C.byref(nw), C.byref(nt))
             cap = int(nt.value)
-        out = np.zeros(max(cap, 1), CAND_DTYPE)
+        out = np.empty(max(cap, 1), CAND_DTYPE)
         rc = _lib.fstat_candidates_get(self._h, out.ctypes.data_as(P(fstat_candidate)), cap,
                                        C.byref(nw), C.byref(nt))
         if rc not in (FSTAT_OK, FSTAT_ERR_OVERFLOW):
             self._raise(rc, "fstat_candidates_get")
-        return out[:nw.value].copy(), int(nt.value)
+        return (out if nw.value == out.size else out[:nw.value].copy()), int(nt.value)
 
     def candidates_get_status(self, cap: int):
         nw, nt = i64(), i64()
