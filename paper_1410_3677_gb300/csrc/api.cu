@@ -330,7 +330,19 @@ void create_impl(Plan &p, const fstat_plan_desc *d) {
         p.n_workers = 1;
         p.cell_batch = 1;
     }
-    size_t scratch_bytes = std::max<size_t>((size_t)p.n_workers * p.cell_batch * 2 * max_nfft * tsz,
+    // a worker's slot holds a launch's cells, or the ring of the fused launch
+    if (fp32) {
+        if (const char *v = getenv("FSTAT_FUSED")) p.fused = atoi(v) != 0;
+        if (const char *v = getenv("FSTAT_FUSED_SLOTS")) p.fused_slots = std::max(2, std::min(256, atoi(v)));
+        if (const char *v = getenv("FSTAT_FUSED_AHEAD")) p.fused_ahead = std::max(1, std::min(p.fused_slots - 1, atoi(v)));
+        if (const char *v = getenv("FSTAT_FUSED_TPI")) {
+            int t = 1;
+            while (2 * t <= std::min(64, atoi(v))) t *= 2;
+            p.fused_tpi = t;
+        }
+    }
+    p.slot_cells = (size_t)std::max<int64_t>(p.cell_batch, fp32 ? p.fused_slots : 1);
+    size_t scratch_bytes = std::max<size_t>((size_t)p.n_workers * p.slot_cells * 2 * max_nfft * tsz,
                                             (size_t)2 * std::max<int64_t>(max_m, p.n_max) * sizeof(double2) * 2);
     if (fp32) {
         if (const char *v = getenv("FSTAT_PERSIST_BATCH")) p.pbatch = std::max(1, atoi(v));
@@ -344,6 +356,7 @@ void create_impl(Plan &p, const fstat_plan_desc *d) {
         if (const char *v = getenv("FSTAT_PERSISTENT")) p.use_persistent = atoi(v) != 0;
         if (const char *v = getenv("FSTAT_ELEMS_PER_THREAD")) p.elems_per_thread = atoi(v) == 8 ? 8 : 16;
         if (const char *v = getenv("FSTAT_ENGINE")) p.engine = atoi(v) == 1 ? 1 : 2;
+        p.fctl = dalloc<uint32_t>(p, (size_t)p.n_workers * (1 + 2 * (size_t)p.cell_batch), n_alloc);
     }
     p.scratch = dalloc<unsigned char>(p, scratch_bytes, n_alloc);
     p.bw_elems = 2 * p.n_max + 2 * max_m;
@@ -466,7 +479,8 @@ void search_impl(Plan &p, int64_t begin, int64_t end) {
     if (p.qerr) check(cudaMemsetAsync(p.qerr, 0, sizeof(uint32_t), s), "memset");
     const int64_t per_band = d.n_sky * d.n_spin;
     const int NW = (int)p.workers.size();
-    const size_t slot_bytes = (size_t)p.cell_batch * 2 * (size_t)p.n_fft_max * (fp32 ? 8 : 16);
+    const size_t slot_bytes = p.slot_cells * 2 * (size_t)p.n_fft_max * (fp32 ? 8 : 16);
+    const size_t ctl_words = 1 + 2 * (size_t)p.cell_batch;
     // the plan's stream waits for every worker stream
     auto join_workers = [&]() {
         if (NW < 2) return;
@@ -498,6 +512,7 @@ void search_impl(Plan &p, int64_t begin, int64_t end) {
         const int i_p1 = stat_index(p, fp32 ? "fft_pass1_f32" : "fft_pass1_f64");
         const int i_p2 = stat_index(p, fp32 ? "fft_pass2_fstat_f32" : "fft_pass2_fstat_f64");
         const int i_pp = stat_index(p, "fft_fstat_persistent_f32");
+        const int i_fu = stat_index(p, "fft_fused_f32");
         const double welem = fp32 ? 16.0 : 32.0;
         for (int64_t sb = s_first; sb <= s_last; sb += p.sky_batch, ++q) {
             const int par = (int)(q & 1);
@@ -534,12 +549,27 @@ void search_impl(Plan &p, int64_t begin, int64_t end) {
                 for (int i = 0; i < NW; ++i)
                     check(cudaStreamWaitEvent(p.workers[i], p.ev_geo[par], 0), "stream wait");
             }
+            const bool fused = fp32 && fused_supported(p, b.logn);
             for (int64_t c = c_lo; c < c_hi; c += p.cell_batch, ++cbi) {
                 const int wi = (int)(cbi % NW);
                 cudaStream_t ws = p.workers[wi];
-                const CellBufs cbuf{p.wbuf[par], p.normbuf[par],
-                                    static_cast<unsigned char *>(p.scratch) + wi * slot_bytes};
                 const int64_t nc = std::min<int64_t>(p.cell_batch, c_hi - c);
+                CellBufs cbuf{p.wbuf[par], p.normbuf[par],
+                              static_cast<unsigned char *>(p.scratch) + wi * slot_bytes};
+                if (fused) {
+                    cbuf.ctl = p.fctl + wi * ctl_words;
+                    check(cudaMemsetAsync(cbuf.ctl, 0, (1 + 2 * (size_t)nc) * sizeof(uint32_t), ws), "memset");
+                    const int64_t sky_a = c / d.n_spin, sky_b = (c + nc - 1) / d.n_spin;
+                    const bool tf = stat_launch(p, i_fu, 2.0 * nc * 5.0 * nfft * (lg1 + lg2),
+                                                (double)(sky_b - sky_a + 1) * b.n * welem);
+                    cudaEvent_t e0 = nullptr, e1 = nullptr;
+                    if (tf) { e0 = ev_get(p); e1 = ev_get(p); check(cudaEventRecord(e0, ws), "event"); }
+                    const int L = launch_search_cells_f32(p, bi, b, sb, c, nc, ws, nullptr, cbuf);
+                    if (L < 0) throw std::string("unsupported transform length");
+                    p.launches += L;
+                    if (tf) { check(cudaEventRecord(e1, ws), "event"); p.pending.push_back({i_fu, e0, e1}); }
+                    continue;
+                }
                 // 5 N log2 N per complex transform, split between the passes; two
                 // transforms per cell.  Pass 1 reads w once per distinct sky.
                 const int64_t sky_a = c / d.n_spin, sky_b = (c + nc - 1) / d.n_spin;

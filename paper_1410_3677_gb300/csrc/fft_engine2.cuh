@@ -45,6 +45,28 @@ __host__ __device__ constexpr double w32_im(int k) {   // -sin(2 pi k / 32)
 template <int R, int DIR, typename T>
 __device__ __forceinline__ void dft(T *re, T *im);
 
+// x <- x W_32^e (DIR = -1) or x conj(W_32^e), e known at compile time once the
+// callers' loops are unrolled: the quarter turns are swaps and negations, so
+// no multiplication by 0 or 1 is left for the compiler to keep.
+template <int DIR, typename T>
+__device__ __forceinline__ void mul_w32(int e, T &xr, T &xi) {
+    e &= 31;
+    if (e == 0) return;
+    if (e == 16) { xr = -xr; xi = -xi; return; }
+    if (e == 8 || e == 24) {   // W = -i (e = 8) or +i (e = 24); conjugated for DIR > 0
+        const bool minus_i = (e == 8) == (DIR < 0);
+        const T r = xr;
+        xr = minus_i ? xi : -xi;
+        xi = minus_i ? -r : r;
+        return;
+    }
+    const T wr = (T)w32_re(e);
+    const T wi = DIR < 0 ? (T)w32_im(e) : -(T)w32_im(e);
+    const T r = xr * wr - xi * wi;
+    xi = xr * wi + xi * wr;
+    xr = r;
+}
+
 // Radix-4 decimation in time: 4 sub-DFTs of length R/4 over x[4m + q], then for
 // each k < R/4 the twiddles W_R^{q k} and a 4-point DFT across q.
 template <int R, int DIR, typename T>
@@ -63,11 +85,9 @@ __device__ __forceinline__ void dft_r4(T *re, T *im) {
         zr[0] = sr[0][k]; zi[0] = si[0][k];
 #pragma unroll
         for (int q = 1; q < 4; ++q) {
-            const int e = (32 / R) * q * k;   // W_R^{q k} = W_32^{(32/R) q k}
-            const T wr = (T)w32_re(e);
-            const T wi = DIR < 0 ? (T)w32_im(e) : -(T)w32_im(e);
-            zr[q] = sr[q][k] * wr - si[q][k] * wi;
-            zi[q] = sr[q][k] * wi + si[q][k] * wr;
+            zr[q] = sr[q][k];
+            zi[q] = si[q][k];
+            mul_w32<DIR>((32 / R) * q * k, zr[q], zi[q]);   // W_R^{q k} = W_32^{(32/R) q k}
         }
         eng::dft4<DIR>(zr[0], zi[0], zr[1], zi[1], zr[2], zi[2], zr[3], zi[3]);
 #pragma unroll
@@ -79,6 +99,30 @@ template <int R, int DIR, typename T>
 __device__ __forceinline__ void dft(T *re, T *im) {
     if constexpr (R == 32 || R == 16) dft_r4<R, DIR>(re, im);
     else eng::dft<R, DIR>(re, im);
+}
+
+// R-point DFT of x[0 .. R/2) with x[R/2 .. R) = 0: the even outputs are the
+// R/2-point DFT of x, the odd ones that of x_r W_R^r (the first radix-2 layer
+// of a decimation in frequency, whose partners are all zero).
+template <int R, int DIR, typename T>
+__device__ __forceinline__ void dft_half_zero(T *re, T *im) {
+    constexpr int H = R / 2;
+    T er[H], ei[H], orr[H], oi[H];
+#pragma unroll
+    for (int r = 0; r < H; ++r) {
+        er[r] = re[r]; ei[r] = im[r];
+        orr[r] = re[r]; oi[r] = im[r];
+        mul_w32<DIR>((32 / R) * r, orr[r], oi[r]);
+    }
+    if constexpr (H > 1) {
+        dft<H, DIR>(er, ei);
+        dft<H, DIR>(orr, oi);
+    }
+#pragma unroll
+    for (int p = 0; p < H; ++p) {
+        re[2 * p] = er[p]; im[2 * p] = ei[p];
+        re[2 * p + 1] = orr[p]; im[2 * p + 1] = oi[p];
+    }
 }
 
 // ------------------------------------------------------------------ plan
@@ -148,7 +192,10 @@ __device__ __forceinline__ void fill_twiddles(typename Vec2T<T>::type *tws, cons
 // One pass over a tile.  LD::load<R0, M/R0>(job, re, im) yields the elements
 // j + r M/R0 of sequence (t, f); ST::store<R, JPF>(job, re, im) receives outputs
 // j + r JPF (R = R1, JPF = R0 after two stages; R = M, JPF = 1 after one).
-template <typename T, int M, int SEQ, int EH, int DIR, int MAPM, class LD, class ST>
+// ZH: the stage-0 inputs r >= R0/2 (sequence elements >= M/2) are known to be
+// zero (the zero padding of a transform at least twice the series): the loader
+// is asked for R0/2 elements and the first DFT skips its zero half.
+template <typename T, int M, int SEQ, int EH, int DIR, int MAPM, class LD, class ST, bool ZH = false>
 __device__ __forceinline__ void run_pass(LD &ld, ST &st, const T *__restrict__ tw) {
     using V = typename Vec2T<T>::type;
     constexpr int R0 = radix0(M), R1 = radix1(M);
@@ -165,10 +212,14 @@ __device__ __forceinline__ void run_pass(LD &ld, ST &st, const T *__restrict__ t
     if constexpr (R1 > 1) __syncthreads();
 
     T re[EH], im[EH];
+    constexpr int RL0 = ZH ? R0 / 2 : R0;   // stage-0 inputs that can be non-zero
 #pragma unroll
-    for (int i = 0; i < NJ0; ++i) ld.template load<R0, JPF0>(job<MAPM, SEQ, TPF, THREADS>(i), &re[i * R0], &im[i * R0]);
+    for (int i = 0; i < NJ0; ++i) ld.template load<RL0, JPF0>(job<MAPM, SEQ, TPF, THREADS>(i), &re[i * R0], &im[i * R0]);
 #pragma unroll
-    for (int i = 0; i < NJ0; ++i) dft<R0, DIR>(&re[i * R0], &im[i * R0]);
+    for (int i = 0; i < NJ0; ++i) {
+        if constexpr (ZH) dft_half_zero<R0, DIR>(&re[i * R0], &im[i * R0]);
+        else dft<R0, DIR>(&re[i * R0], &im[i * R0]);
+    }
     if constexpr (R1 == 1) {
 #pragma unroll
         for (int i = 0; i < NJ0; ++i) st.template store<R0, JPF0>(job<MAPM, SEQ, TPF, THREADS>(i), &re[i * R0], &im[i * R0]);

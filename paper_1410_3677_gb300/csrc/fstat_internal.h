@@ -13,6 +13,10 @@
 namespace fstat {
 
 constexpr int kMinLogN = 8;    // n_fft >= 256
+// Fused FP32 launch: scratch slots in its ring, and how many cells pass 2 trails
+// pass 1 by (defaults).
+constexpr int kFusedSlots = 16;
+constexpr int kFusedAhead = 6;
 constexpr int kMaxLogN = 20;   // n_fft <= 2^20
 
 // Split of a power-of-two transform length N = N1 * N2 into the two passes of
@@ -98,7 +102,8 @@ struct Plan {
     int64_t pbatch = 2, pslots = 8;
     uint32_t *queue = nullptr;     // [head | done1[nb] | done2[nb]]
     uint32_t *qerr = nullptr;      // error word (bit 0: a bounded wait ran out)
-    int64_t withhold_item = -1;    // test hook (FSTAT_TEST_WITHHOLD_ITEM)
+    int64_t withhold_item = -1;    // test hook (FSTAT_TEST_WITHHOLD_ITEM): the persistent kernel's queue
+                                   // item, or the cell whose pass 1 never reports in the fused launch
     bool use_persistent = false;   // FSTAT_PERSISTENT=1: one queue-fed launch per sky batch
     // worker streams of the batched FP32 passes, each with its own scratch slot
     int n_workers = 1;
@@ -108,6 +113,11 @@ struct Plan {
     std::vector<cudaEvent_t> ev_join;
     int elems_per_thread = 16;     // FP32 batched passes: 16 or 8 complex elements per thread
     int engine = 2;                // FP32 batched passes, 2^12 .. 2^19: 2 = two-stage engine, 1 = radix-8 engine
+    bool fused = false;            // two-stage engine: both passes in one ticket-ordered launch
+    uint32_t *fctl = nullptr;      // per worker: 1 + 2 * cell_batch counters of the fused launch
+    size_t slot_cells = 0;         // cells of scratch per worker (>= cell_batch, >= the fused ring)
+    int fused_slots = kFusedSlots, fused_ahead = kFusedAhead;
+    int fused_tpi = 4;             // tiles per ticket of the fused launch (power of two)
 
     // Bluestein / generic-FFT work buffers (double2)
     double *bw = nullptr;
@@ -152,6 +162,7 @@ struct CellBufs {
     const void *w;
     const double *norm;
     void *scratch;
+    uint32_t *ctl = nullptr;   // fused launch: ticket + per-cell counters (1 + 2 * cell_batch), zeroed
 };
 
 // ---------------------------------------------------------------- launchers
@@ -196,6 +207,8 @@ int persistent_tiles_per_cell(int logn);
 int launch_search_persistent(const Plan &p, int band_idx, const BandDev &b, int64_t s0,
                              int64_t c_lo, int64_t c_hi, cudaStream_t s, const CellBufs &cb);
 
+// Whether the FP32 cells of a band of length 2^logn run as one fused launch.
+bool fused_supported(const Plan &p, int logn);
 // `mid` (may be null) is recorded between the two passes.
 int launch_search_cells_f32(const Plan &p, int band_idx, const BandDev &b, int64_t s0,
                             int64_t c0, int64_t nc, cudaStream_t s, cudaEvent_t mid,

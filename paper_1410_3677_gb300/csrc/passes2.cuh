@@ -11,6 +11,7 @@
 
 #include "fft_engine2.cuh"
 #include "fstat_internal.h"
+#include "sync_ptx.cuh"
 
 namespace fstat {
 
@@ -48,12 +49,13 @@ struct SearchLoad2 {
     const float2 *ws;
     uint64_t afx;
     int k1_0;
-    __device__ void init() {
-        const int64_t c = c0 + blockIdx.y;
+    // tile: column block; cell: cell of the launch; slot: scratch slot
+    __device__ void init(int tile, int64_t cell, int64_t) {
+        const int64_t c = c0 + cell;
         const int64_t sky = c / n_spin;
         ws = reinterpret_cast<const float2 *>(w + (sky - s0) * w_stride);
         afx = chirp[c - sky * n_spin];
-        k1_0 = blockIdx.x * C::F;
+        k1_0 = tile * C::F;
     }
     template <int R, int JPF>
     __device__ __forceinline__ void load(const eng2::Job &q, float *re, float *im) const {
@@ -84,16 +86,18 @@ struct SearchLoad2 {
 
 // Pass 1 output: twiddle W_N^{k1 l2}, l2 = j + r JPF, as W^{k1 j} (W^{k1 JPF})^r
 // (two lookups W_N^m = hi[m >> log N1] lo[m & (N1 - 1)] per job), then the
-// transposed store A_t[l2][k1] into scratch slot blockIdx.y.
+// transposed store A_t[l2][k1] into the cell's scratch slot.  Scratch is written
+// and read through L2 only (st.global.cg / ld.global.cg): it is streamed once
+// each way, and a slot reused within one launch never meets a stale L1 line.
 template <class C>
 struct ScratchStore2 {
     float2 *scratch;
     const float *lo, *hi;
     float2 *base;
     int k1_0;
-    __device__ void init() {
-        base = scratch + (int64_t)blockIdx.y * 2 * C::N;
-        k1_0 = blockIdx.x * C::F;
+    __device__ void init(int tile, int64_t, int64_t slot) {
+        base = scratch + slot * 2 * C::N;
+        k1_0 = tile * C::F;
     }
     __device__ __forceinline__ float2 wn(int m) const {
         const float2 th = __ldg(reinterpret_cast<const float2 *>(hi) + (m >> C::LOGN1));
@@ -109,28 +113,28 @@ struct ScratchStore2 {
 #pragma unroll
         for (int r = 0; r < R; ++r) {
             const float xr = re[r], xi = im[r];
-            dst[(int64_t)r * JPF * C::N1] = float2{xr * w.x - xi * w.y, xr * w.y + xi * w.x};
+            __stcg(dst + (int64_t)r * JPF * C::N1, float2{xr * w.x - xi * w.y, xr * w.y + xi * w.x});
             if (r + 1 < R) w = float2{w.x * st.x - w.y * st.y, w.x * st.y + w.y * st.x};
         }
     }
 };
 
-// Pass 2 input: row l2 of transform t from scratch slot blockIdx.y.
+// Pass 2 input: row l2 of transform t from the cell's scratch slot.
 template <class C>
 struct ScratchLoad2 {
     const float2 *scratch;
     const float2 *base;
     int l2_0;
-    __device__ void init() {
-        base = scratch + (int64_t)blockIdx.y * 2 * C::N;
-        l2_0 = blockIdx.x * C::F;
+    __device__ void init(int tile, int64_t, int64_t slot) {
+        base = scratch + slot * 2 * C::N;
+        l2_0 = tile * C::F;
     }
     template <int R, int JPF>
     __device__ __forceinline__ void load(const eng2::Job &q, float *re, float *im) const {
         const float2 *row = base + (int64_t)q.t * C::N + (int64_t)(l2_0 + q.f) * C::N1 + q.j;
 #pragma unroll
         for (int r = 0; r < R; ++r) {
-            const float2 v = row[r * JPF];
+            const float2 v = __ldcg(row + r * JPF);
             re[r] = v.x; im[r] = v.y;
         }
     }
@@ -157,13 +161,13 @@ struct SearchEpi2 {
     float na, nb, thr_half;
     uint32_t cell;
     int l2_0;
-    __device__ void init() {
-        const int64_t c = c0 + blockIdx.y;
+    __device__ void init(int tile, int64_t cl, int64_t) {
+        const int64_t c = c0 + cl;
         const int64_t sky = c / n_spin;
         na = (float)norm[2 * (sky - s0)];
         nb = (float)norm[2 * (sky - s0) + 1];
         cell = cell_base + (uint32_t)c;
-        l2_0 = blockIdx.x * C::F;
+        l2_0 = tile * C::F;
         thr_half = 0.5f * thr;   // 2F > thr  <=>  F > thr / 2, both sides exact
     }
     template <int R, int JPF>
@@ -206,14 +210,126 @@ struct SearchEpi2 {
     }
 };
 
-// Pass 2 holds fewer live values (no demodulation, no twiddle powers) and fits
-// three CTAs per SM (<= 85 registers, 3 x 68 KB of shared memory); pass 1 two.
+// Three CTAs per SM: <= 85 registers (pass 1 loads half its column, pass 2
+// keeps no demodulation or twiddle-power state) and 3 x 68 KB of shared memory.
+// Pass 1 of a search transform (N_fft >= 2n) reads only the first half of each
+// column: elements k2 >= N2/2 lie at k >= N/2 >= n, in the zero padding.
 template <int LOGN, int PASS, int MAPM, class LD, class ST>
-__global__ void __launch_bounds__(256, PASS == 2 ? 3 : 2) k_pass2(LD ld, ST st, const float *__restrict__ tw) {
+__global__ void __launch_bounds__(256, 3) k_pass2(LD ld, ST st, const float *__restrict__ tw) {
     using C = Cfg2<LOGN, PASS>;
-    ld.init();
-    st.init();
-    eng2::run_pass<float, C::M, C::SEQ, C::EH, -1, MAPM>(ld, st, tw);
+    ld.init(blockIdx.x, blockIdx.y, blockIdx.y);
+    st.init(blockIdx.x, blockIdx.y, blockIdx.y);
+    eng2::run_pass<float, C::M, C::SEQ, C::EH, -1, MAPM, LD, ST, PASS == 1>(ld, st, tw);
+}
+
+// ------------------------------------------------------------------ fused launch
+// Both passes of a batch of cells in one launch.  Every CTA takes the next item
+// from a ticket counter; items run in the order
+//   step s: the T1 pass-1 tiles of cell s, then the T2 pass-2 tiles of cell s - A
+// (A = ahead), so pass 2 of a cell starts A cells after its pass 1 and the
+// cell's intermediate is still in L2.  Cells use a ring of S > A scratch slots
+// (4 MiB each at N = 2^18, resident in L2).  Pass 2 of cell c waits for the T1
+// pass-1 tiles of c; pass 1 of cell c waits until pass 2 of cell c - S has
+// released the slot.  A CTA publishes its completion the way a grid-wide
+// barrier does: CTA barrier, then one thread's fence and release increment.  Both waited-on items carry smaller tickets than the
+// waiter, so they belong to CTAs already running, whatever the order in which
+// the hardware starts CTAs: every wait ends.  Waits are still bounded (1 s of
+// global time); one that runs out sets the error flag, and every later wait
+// sees the flag and gives up at once.
+struct FusedCtl {
+    uint32_t *ticket;   // next item
+    uint32_t *done1;    // [nc] pass-1 tiles finished per cell
+    uint32_t *done2;    // [nc] pass-2 tiles finished per cell
+    uint32_t *err;      // non-zero after a wait ran out
+    int64_t nc;         // cells in the launch
+    int slots, ahead;   // ring slots S > ahead A
+    int tpi;            // tiles per item (a power of two dividing both passes' tile counts)
+    int64_t withhold;   // test hook: this cell's pass 1 never reports completion (-1: none)
+};
+
+__device__ __forceinline__ bool fused_wait(const uint32_t *cnt, uint32_t target, uint32_t *err) {
+    if (ptx::ld_acquire(cnt) >= target) return true;
+    const uint64_t t0 = ptx::globaltimer_ns();
+    for (;;) {
+        if (*reinterpret_cast<volatile uint32_t *>(err)) return false;
+        if (ptx::ld_acquire(cnt) >= target) return true;
+        if (ptx::globaltimer_ns() - t0 > 1000000000ull) {
+            atomicExch(err, 1u);
+            return false;
+        }
+        __nanosleep(100);
+    }
+}
+
+// Persistent: the grid holds as many CTAs as fit on the GPU, each looping over
+// tickets; the next ticket is claimed while the current item runs, so its
+// latency is hidden.  A CTA holding a claimed ticket is running, which keeps the
+// argument above valid.
+template <int LOGN, bool LOWER>
+__global__ void __launch_bounds__(256, 3)
+k_search_fused(SearchLoad2<Cfg2<LOGN, 1>> ld1, ScratchStore2<Cfg2<LOGN, 1>> st1,
+               ScratchLoad2<Cfg2<LOGN, 2>> ld2, SearchEpi2<Cfg2<LOGN, 2>, LOWER> st2,
+               const float *__restrict__ tw_in1, const float *__restrict__ tw_in2, FusedCtl ctl) {
+    using C1 = Cfg2<LOGN, 1>;
+    using C2 = Cfg2<LOGN, 2>;
+    constexpr int T1 = C1::TILES, T2 = C2::TILES;
+    const int tpi = ctl.tpi;
+    const int I1 = T1 / tpi, I2 = T2 / tpi;          // items per cell and pass
+    const int64_t total = (ctl.nc + ctl.ahead) * (int64_t)(I1 + I2);
+    __shared__ uint32_t s_item, s_next;
+    __shared__ int s_go;
+    if (threadIdx.x == 0) s_item = atomicAdd(ctl.ticket, 1u);
+    __syncthreads();
+    for (;;) {
+        const int64_t item = s_item;
+        if (item >= total) return;                   // the same for the whole CTA
+        const int64_t step = item / (I1 + I2);
+        const int r = (int)(item - step * (I1 + I2));
+        const bool p1 = r < I1;
+        const int64_t cell = p1 ? step : step - ctl.ahead;
+        const bool valid = cell >= 0 && cell < ctl.nc;
+        const int64_t slot = valid ? cell % ctl.slots : 0;
+        if (threadIdx.x == 0) {
+            s_next = atomicAdd(ctl.ticket, 1u);
+            bool ok = true;
+            if (valid) {
+                if (!p1) ok = fused_wait(ctl.done1 + cell, T1, ctl.err);
+                else if (cell >= ctl.slots) ok = fused_wait(ctl.done2 + (cell - ctl.slots), T2, ctl.err);
+            }
+            s_go = !ok ? -1 : (valid ? 1 : 0);
+        }
+        __syncthreads();
+        const int go = s_go;
+        if (go < 0) return;                          // a wait gave up: every later wait will too
+        if (go) {
+            if (p1) {
+#pragma unroll 1
+                for (int u = 0; u < tpi; ++u) {
+                    if (u) __syncthreads();              // the previous tile's exchange is read
+                    ld1.init(r * tpi + u, cell, slot);
+                    st1.init(r * tpi + u, cell, slot);
+                    eng2::run_pass<float, C1::M, C1::SEQ, C1::EH, -1, eng2::kMapFJ, SearchLoad2<C1>,
+                                   ScratchStore2<C1>, true>(ld1, st1, tw_in2);
+                }
+            } else {
+#pragma unroll 1
+                for (int u = 0; u < tpi; ++u) {
+                    if (u) __syncthreads();
+                    ld2.init((r - I1) * tpi + u, cell, slot);
+                    st2.init((r - I1) * tpi + u, cell, slot);
+                    eng2::run_pass<float, C2::M, C2::SEQ, C2::EH, -1, eng2::kMapW, ScratchLoad2<C2>,
+                                   SearchEpi2<C2, LOWER>, false>(ld2, st2, tw_in1);
+                }
+            }
+            __syncthreads();
+            if (threadIdx.x == 0 && !(p1 && cell == ctl.withhold)) {
+                __threadfence();
+                ptx::red_release_add(p1 ? ctl.done1 + cell : ctl.done2 + cell, (uint32_t)tpi);
+            }
+        }
+        if (threadIdx.x == 0) s_item = s_next;
+        __syncthreads();
+    }
 }
 
 }  // namespace fstat

@@ -1,6 +1,9 @@
 // FP32 instantiations of the search passes (FSTAT_FP32_BATCHED): the two-stage
-// engine for transform lengths 2^12 .. 2^19, the radix-8 engine otherwise (and
-// whenever the plan selects it).
+// engine for transform lengths 2^12 .. 2^19 (both passes in one ticket-ordered
+// launch, or as two launches), the radix-8 engine otherwise (and whenever the
+// plan selects it).
+#include <algorithm>
+
 #include "passes2.cuh"
 #include "search_launch.cuh"
 
@@ -8,11 +11,9 @@ namespace fstat {
 namespace {
 
 template <int LOGN, bool LOWER>
-void launch_pass2(const Plan &p, int band_idx, const BandDev &b, int64_t s0, int64_t c0, int64_t nc,
-                  cudaStream_t s, const CellBufs &cb, const ScratchLoad2<Cfg2<LOGN, 2>> &ld2,
-                  const float *tw_in1) {
-    using C2 = Cfg2<LOGN, 2>;
-    SearchEpi2<C2, LOWER> st2{};
+SearchEpi2<Cfg2<LOGN, 2>, LOWER> make_epi(const Plan &p, int band_idx, const BandDev &b, int64_t c0,
+                                          int64_t s0, const CellBufs &cb) {
+    SearchEpi2<Cfg2<LOGN, 2>, LOWER> st2{};
     st2.norm = cb.norm;
     st2.n_spin = (int)p.desc.n_spin;
     st2.c0 = c0;
@@ -24,10 +25,56 @@ void launch_pass2(const Plan &p, int band_idx, const BandDev &b, int64_t s0, int
     st2.out = p.cand;
     st2.count = p.cand_count;
     st2.cap = (unsigned long long)p.cand_capacity;
+    return st2;
+}
+
+template <int LOGN, bool LOWER>
+int launch_two(const Plan &p, int band_idx, const BandDev &b, int64_t s0, int64_t c0, int64_t nc,
+               cudaStream_t s, cudaEvent_t mid, const CellBufs &cb, const SearchLoad2<Cfg2<LOGN, 1>> &ld1,
+               const ScratchStore2<Cfg2<LOGN, 1>> &st1, const ScratchLoad2<Cfg2<LOGN, 2>> &ld2,
+               const TwiddleSet *tw) {
+    using C1 = Cfg2<LOGN, 1>;
+    using C2 = Cfg2<LOGN, 2>;
+    auto k1 = k_pass2<LOGN, 1, eng2::kMapFJ, SearchLoad2<C1>, ScratchStore2<C1>>;
+    static bool attr1 = false;
+    if (!attr1) { set_smem(k1, C1::SMEM); attr1 = true; }
+    k1<<<dim3(C1::TILES, (unsigned)nc), C1::THREADS, C1::SMEM, s>>>(ld1, st1, tw->in2_f);
+    if (mid) cudaEventRecord(mid, s);
+    const auto st2 = make_epi<LOGN, LOWER>(p, band_idx, b, c0, s0, cb);
     auto k2 = k_pass2<LOGN, 2, eng2::kMapW, ScratchLoad2<C2>, SearchEpi2<C2, LOWER>>;
     static bool attr2 = false;
     if (!attr2) { set_smem(k2, C2::SMEM); attr2 = true; }
-    k2<<<dim3(C2::TILES, (unsigned)nc), C2::THREADS, C2::SMEM, s>>>(ld2, st2, tw_in1);
+    k2<<<dim3(C2::TILES, (unsigned)nc), C2::THREADS, C2::SMEM, s>>>(ld2, st2, tw->in1_f);
+    return 2;
+}
+
+template <int LOGN, bool LOWER>
+int launch_fused(const Plan &p, int band_idx, const BandDev &b, int64_t s0, int64_t c0, int64_t nc,
+                 cudaStream_t s, const CellBufs &cb, const SearchLoad2<Cfg2<LOGN, 1>> &ld1,
+                 const ScratchStore2<Cfg2<LOGN, 1>> &st1, const ScratchLoad2<Cfg2<LOGN, 2>> &ld2,
+                 const TwiddleSet *tw) {
+    using C1 = Cfg2<LOGN, 1>;
+    using C2 = Cfg2<LOGN, 2>;
+    const auto st2 = make_epi<LOGN, LOWER>(p, band_idx, b, c0, s0, cb);
+    // counters zeroed by the caller; the test hook names a plan-wide item (cell)
+    const int64_t wh = p.withhold_item >= c0 && p.withhold_item < c0 + nc ? p.withhold_item - c0 : -1;
+    const int tpi = std::min(p.fused_tpi, std::min(C1::TILES, C2::TILES));
+    FusedCtl ctl{cb.ctl, cb.ctl + 1, cb.ctl + 1 + nc, p.qerr, nc, p.fused_slots, p.fused_ahead, tpi, wh};
+    constexpr size_t smem = C1::SMEM > C2::SMEM ? C1::SMEM : C2::SMEM;
+    auto k = k_search_fused<LOGN, LOWER>;
+    static int resident = 0;   // CTAs of this kernel that fit on the device at once
+    if (!resident) {
+        set_smem(k, smem);
+        int dev = 0, sms = 0, per_sm = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, 256, smem);
+        resident = std::max(1, sms * std::max(per_sm, 1));
+    }
+    const int64_t items = (nc + p.fused_ahead) * (int64_t)(C1::TILES / tpi + C2::TILES / tpi);
+    const unsigned grid = (unsigned)std::min<int64_t>(items, resident);
+    k<<<grid, 256, smem, s>>>(ld1, st1, ld2, st2, tw->in1_f, tw->in2_f, ctl);
+    return 1;
 }
 
 template <int LOGN>
@@ -50,20 +97,20 @@ int launch_search2(const Plan &p, int band_idx, const BandDev &b, int64_t s0, in
     st1.scratch = reinterpret_cast<float2 *>(cb.scratch);
     st1.lo = tw->lo_f;
     st1.hi = tw->hi_f;
-    auto k1 = k_pass2<LOGN, 1, eng2::kMapFJ, SearchLoad2<C1>, ScratchStore2<C1>>;
-    static bool attr1 = false;
-    if (!attr1) { set_smem(k1, C1::SMEM); attr1 = true; }
-    k1<<<dim3(C1::TILES, (unsigned)nc), C1::THREADS, C1::SMEM, s>>>(ld1, st1, tw->in2_f);
-    if (mid) cudaEventRecord(mid, s);
-
     ScratchLoad2<C2> ld2{};
     ld2.scratch = reinterpret_cast<const float2 *>(cb.scratch);
-    if (b.hi < (int64_t)C2::N / 2) launch_pass2<LOGN, true>(p, band_idx, b, s0, c0, nc, s, cb, ld2, tw->in1_f);
-    else launch_pass2<LOGN, false>(p, band_idx, b, s0, c0, nc, s, cb, ld2, tw->in1_f);
-    return 2;
+    const bool lower = b.hi < (int64_t)C2::N / 2;
+    if (fused_supported(p, LOGN) && cb.ctl) {
+        return lower ? launch_fused<LOGN, true>(p, band_idx, b, s0, c0, nc, s, cb, ld1, st1, ld2, tw)
+                     : launch_fused<LOGN, false>(p, band_idx, b, s0, c0, nc, s, cb, ld1, st1, ld2, tw);
+    }
+    return lower ? launch_two<LOGN, true>(p, band_idx, b, s0, c0, nc, s, mid, cb, ld1, st1, ld2, tw)
+                 : launch_two<LOGN, false>(p, band_idx, b, s0, c0, nc, s, mid, cb, ld1, st1, ld2, tw);
 }
 
 }  // namespace
+
+bool fused_supported(const Plan &p, int logn) { return p.engine == 2 && p.fused && logn >= 12 && logn <= 19; }
 
 int launch_search_cells_f32(const Plan &p, int band_idx, const BandDev &b, int64_t s0,
                             int64_t c0, int64_t nc, cudaStream_t s, cudaEvent_t mid,

@@ -42,7 +42,9 @@ def _run(fs, w, thr, env=None, **kw):
 
 
 R8 = {"FSTAT_PERSISTENT": "0", "FSTAT_ENGINE": "1"}     # radix-8 engine, two launches per batch
-TWO = {"FSTAT_PERSISTENT": "0"}                           # default: two-stage engine
+TWO = {"FSTAT_PERSISTENT": "0", "FSTAT_FUSED": "0"}      # two-stage engine, two launches per batch
+DEFAULT = {"FSTAT_PERSISTENT": "0"}                       # the default (the same)
+FUSED = {"FSTAT_PERSISTENT": "0", "FSTAT_FUSED": "1"}    # two-stage engine, one ticket-ordered launch
 
 
 @pytest.mark.parametrize("base,env", [
@@ -51,12 +53,19 @@ TWO = {"FSTAT_PERSISTENT": "0"}                           # default: two-stage e
     (R8, {"FSTAT_PERSISTENT": "1", "FSTAT_PERSIST_BATCH": "5", "FSTAT_PERSIST_SLOTS": "8"}),
     (R8, {"FSTAT_ENGINE": "1", "FSTAT_ELEMS_PER_THREAD": "8"}),
     (R8, {"FSTAT_ENGINE": "1", "FSTAT_ELEMS_PER_THREAD": "8", "FSTAT_CELL_BATCH": "7", "FSTAT_STREAMS": "2"}),
-    (TWO, {"FSTAT_CELL_BATCH": "7", "FSTAT_STREAMS": "2"}),
-    (TWO, {"FSTAT_CELL_BATCH": "1", "FSTAT_STREAMS": "3"}),
+    (TWO, {"FSTAT_FUSED": "0", "FSTAT_CELL_BATCH": "7", "FSTAT_STREAMS": "2"}),
+    (TWO, {"FSTAT_FUSED": "0", "FSTAT_CELL_BATCH": "1", "FSTAT_STREAMS": "3"}),
+    (TWO, DEFAULT),
+    (TWO, {"FSTAT_CELL_BATCH": "2"}),
+    (TWO, {"FSTAT_CELL_BATCH": "5", "FSTAT_STREAMS": "2"}),
+    (TWO, FUSED),
+    (TWO, {"FSTAT_FUSED": "1", "FSTAT_CELL_BATCH": "3"}),
+    (TWO, {"FSTAT_FUSED": "1", "FSTAT_CELL_BATCH": "11", "FSTAT_STREAMS": "2"}),
 ])
 def test_launch_shapes_match_bitwise(fs, base, env):
-    """The queue-fed persistent kernel and other tile / batch shapes against the
-    two-launches-per-batch form of the same FFT engine.  Tiny workload (N_fft =
+    """The queue-fed persistent kernel, the fused ticket-ordered launch and other
+    tile / batch shapes against the two-launches-per-batch form of the same FFT
+    engine.  Tiny workload (N_fft =
     2^13) and a two-sidereal-day band (2^18) with cell counts that leave a partial
     last batch."""
     for w in (S.workload(1, n_sky=9, n_spin=3), S.workload(3, n_sky=5, n_spin=3)):
@@ -78,7 +87,7 @@ def test_engines_agree_on_every_bin(fs, n, n_fft):
     b = S.make_band(n, 2.0, 5 + n, 1.0, w0.alpha, w0.delta, w0.fdot, [], n_fft=n_fft)
     w = S.Workload("engines", [b], w0.alpha, w0.delta, w0.fdot, 10.0, upsample=2)
     out = []
-    for env in (R8, TWO):
+    for env in (R8, DEFAULT):
         p, rc, c, total = _run(fs, w, -1.0, env)
         p.close()
         assert rc == fs.FSTAT_OK and total == 6 * (n_fft // 2 - 1)
@@ -112,5 +121,22 @@ def test_withheld_completion_times_out_and_gpu_stays_usable(fs):
     assert p.search_status() == fs.FSTAT_ERR_STATE      # poisoned
     p.close()
     p, rc, c, total = _run(fs, w, 20.0)                 # a fresh plan works
+    p.close()
+    assert rc == fs.FSTAT_OK and total > 0
+
+
+def test_fused_launch_withheld_completion_times_out(fs):
+    """The fused launch with the pass-1 completion of cell 0 withheld (test hook):
+    its pass-2 tiles give up after the bounded wait, every later wait sees the
+    error flag, the search returns FSTAT_ERR_TIMEOUT and the GPU stays usable."""
+    w = S.workload(1, n_sky=8, n_spin=4)
+    t0 = time.time()
+    p, rc, _, _ = _run(fs, w, 20.0, {"FSTAT_FUSED": "1", "FSTAT_TEST_WITHHOLD_ITEM": "0"})
+    elapsed = time.time() - t0
+    assert rc == fs.FSTAT_ERR_TIMEOUT
+    assert elapsed < 30.0
+    assert p.search_status() == fs.FSTAT_ERR_STATE
+    p.close()
+    p, rc, c, total = _run(fs, w, 20.0)
     p.close()
     assert rc == fs.FSTAT_OK and total > 0
