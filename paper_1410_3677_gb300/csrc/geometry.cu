@@ -48,6 +48,25 @@ __device__ double block_sum256(double v, double *sh) {
     return r;
 }
 
+// The same for FP32 terms: each warp adds its 32 terms in FP32 (relative error
+// ~1e-7), the block adds the warp sums in FP64; the blocks' partials are then
+// added with compensation.  The FP32 form's S sums thus keep FP64 accumulation
+// where the term count is large, and spend no FP64 instructions per sample.
+__device__ double block_sum256_f(float v, double *sh) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0) sh[w] = (double)v;
+    __syncthreads();
+    double r = 0.0;
+    if (w == 0) {
+        r = (l < (int)(blockDim.x >> 5)) ? sh[l] : 0.0;
+        r = warp_sum(r);
+    }
+    __syncthreads();
+    return r;
+}
+
 // ------------------------------------------------------------------ sigma^2
 __global__ void __launch_bounds__(256) k_sumsq(const double *__restrict__ x, int64_t n,
                                                double *__restrict__ partials) {
@@ -123,7 +142,8 @@ __global__ void __launch_bounds__(256) k_geometry(GeoArgs g) {
     const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const int sl = blockIdx.y;
     const SkyConst sc = g.sky[g.s0 + sl];
-    double saa = 0.0, sbb = 0.0, sab = 0.0;
+    double saa = 0.0, sbb = 0.0, sab = 0.0;    // FP64 form
+    float saa_f = 0.f, sbb_f = 0.f, sab_f = 0.f;   // FP32 form
     if (k < g.n) {
         // detector time t of barycentric sample k: t = k dt - d(k dt - d(k dt))
         const double *dd = g.d + (int64_t)sl * g.d_stride;
@@ -141,8 +161,6 @@ __global__ void __launch_bounds__(256) k_geometry(GeoArgs g) {
             d2 = delay_lin(dd, g.n, u);
         }
         const bool valid = (u >= 0.0) && (u <= (double)(g.n - 1));
-        const double t = u * g.dt;
-        const double h = sc.alpha - (g.phi0 + kOmegaR * t);
         // Keys cubic (a = -1/2) on the upsampled series, periodic indexing
         const double p = (double)g.U * u;
         const double pf = floor(p);
@@ -161,7 +179,9 @@ __global__ void __launch_bounds__(256) k_geometry(GeoArgs g) {
         const double cyc = __dmul_rn(g.f_off, d2);
         const double fr = __dsub_rn(cyc, floor(cyc));
         if constexpr (FP32) {
-            const float hr = (float)(h - kTwoPi * rint(h * (1.0 / kTwoPi)));
+            // hour angle h = alpha - phi0 - Omega_r t in FP32 (|h| < 20 rad, error
+            // ~1e-6 rad from t = u dt rounded to FP32)
+            const float hr = (float)(sc.alpha - g.phi0) - (float)kOmegaR * ((float)u * (float)g.dt);
             float s1, c1;
             sincosf(hr, &s1, &c1);
             const float c2 = c1 * c1 - s1 * s1, s2 = 2.f * s1 * c1;
@@ -183,9 +203,9 @@ __global__ void __launch_bounds__(256) k_geometry(GeoArgs g) {
                 sincospif(2.f * frs, &sp, &cp);
                 yr = v * cp;
                 yi = -v * sp;
-                saa = (double)av * av;
-                sbb = (double)bv * bv;
-                sab = (double)av * bv;
+                saa_f = av * av;
+                sbb_f = bv * bv;
+                sab_f = av * bv;
             }
             float4 *w = (float4 *)g.w + (int64_t)sl * g.w_stride;
             w[k] = make_float4(yr * av, yi * av, yr * bv, yi * bv);
@@ -194,6 +214,7 @@ __global__ void __launch_bounds__(256) k_geometry(GeoArgs g) {
                 g.dbg_a[k] = av; g.dbg_b[k] = bv; g.dbg_mask[k] = valid;
             }
         } else {
+            const double h = sc.alpha - (g.phi0 + kOmegaR * (u * g.dt));
             double s1, c1;
             sincos(h, &s1, &c1);
             const double c2 = c1 * c1 - s1 * s1, s2 = 2.0 * s1 * c1;
@@ -226,9 +247,16 @@ __global__ void __launch_bounds__(256) k_geometry(GeoArgs g) {
             }
         }
     }
-    const double ta = block_sum256(saa, sh);
-    const double tb = block_sum256(sbb, sh);
-    const double tab = block_sum256(sab, sh);
+    double ta, tb, tab;
+    if constexpr (FP32) {
+        ta = block_sum256_f(saa_f, sh);
+        tb = block_sum256_f(sbb_f, sh);
+        tab = block_sum256_f(sab_f, sh);
+    } else {
+        ta = block_sum256(saa, sh);
+        tb = block_sum256(sbb, sh);
+        tab = block_sum256(sab, sh);
+    }
     if (threadIdx.x == 0) {
         double *o = g.partials + ((int64_t)sl * g.nblk + blockIdx.x) * 3;
         o[0] = ta; o[1] = tb; o[2] = tab;
