@@ -333,6 +333,13 @@ void create_impl(Plan &p, const fstat_plan_desc *d) {
     // a worker's slot holds a launch's cells, or the ring of the fused launch
     if (fp32) {
         if (const char *v = getenv("FSTAT_FUSED")) p.fused = atoi(v) != 0;
+        {   // pass-2 prefetch distance: one CTA per resident slot (3 per SM) ahead
+            int dev = 0, sms = 0;
+            check(cudaGetDevice(&dev), "cudaGetDevice");
+            check(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "device attribute");
+            p.pf_dist = 3 * (int64_t)sms;
+        }
+        if (const char *v = getenv("FSTAT_PF_DIST")) p.pf_dist = std::max(0, atoi(v));
         if (const char *v = getenv("FSTAT_FUSED_SLOTS")) p.fused_slots = std::max(2, std::min(256, atoi(v)));
         if (const char *v = getenv("FSTAT_FUSED_AHEAD")) p.fused_ahead = std::max(1, std::min(p.fused_slots - 1, atoi(v)));
         if (const char *v = getenv("FSTAT_FUSED_TPI")) {

@@ -118,6 +118,7 @@ struct Plan {
     size_t slot_cells = 0;         // cells of scratch per worker (>= cell_batch, >= the fused ring)
     int fused_slots = kFusedSlots, fused_ahead = kFusedAhead;
     int fused_tpi = 4;             // tiles per ticket of the fused launch (power of two)
+    int64_t pf_dist = 0;           // two-stage pass 2: L2 prefetch distance in CTAs (0: off)
 
     // Bluestein / generic-FFT work buffers (double2)
     double *bw = nullptr;

@@ -123,11 +123,27 @@ struct ScratchStore2 {
 template <class C>
 struct ScratchLoad2 {
     const float2 *scratch;
+    int64_t pf_dist;     // two-launch form: prefetch the tile this many CTAs ahead (0: off)
     const float2 *base;
     int l2_0;
     __device__ void init(int tile, int64_t, int64_t slot) {
         base = scratch + slot * 2 * C::N;
         l2_0 = tile * C::F;
+    }
+    // The rows of the tile `pf_dist` CTAs further in launch order go to L2 ahead of
+    // their CTA (two contiguous 32 KB runs, one per transform), so the DRAM reads
+    // of pass 2 run behind its computation instead of at the start of every CTA.
+    __device__ void prefetch_ahead() const {
+        if (pf_dist <= 0 || threadIdx.x != 0) return;
+        const int64_t b = blockIdx.x + (int64_t)gridDim.x * blockIdx.y + pf_dist;
+        const int64_t total = (int64_t)gridDim.x * gridDim.y;
+        if (b >= total) return;
+        const int64_t slot = b / gridDim.x;
+        const int tile = (int)(b - slot * gridDim.x);
+        const float2 *rows = scratch + slot * 2 * C::N + (int64_t)tile * C::F * C::N1;
+        constexpr uint32_t bytes = (uint32_t)(C::F * C::N1 * sizeof(float2));
+        ptx::bulk_prefetch_l2(rows, bytes);
+        ptx::bulk_prefetch_l2(rows + C::N, bytes);
     }
     template <int R, int JPF>
     __device__ __forceinline__ void load(const eng2::Job &q, float *re, float *im) const {
@@ -217,6 +233,7 @@ struct SearchEpi2 {
 template <int LOGN, int PASS, int MAPM, class LD, class ST>
 __global__ void __launch_bounds__(256, 3) k_pass2(LD ld, ST st, const float *__restrict__ tw) {
     using C = Cfg2<LOGN, PASS>;
+    if constexpr (PASS == 2) ld.prefetch_ahead();
     ld.init(blockIdx.x, blockIdx.y, blockIdx.y);
     st.init(blockIdx.x, blockIdx.y, blockIdx.y);
     eng2::run_pass<float, C::M, C::SEQ, C::EH, -1, MAPM, LD, ST, PASS == 1>(ld, st, tw);

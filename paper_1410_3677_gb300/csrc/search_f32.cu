@@ -99,6 +99,7 @@ int launch_search2(const Plan &p, int band_idx, const BandDev &b, int64_t s0, in
     st1.hi = tw->hi_f;
     ScratchLoad2<C2> ld2{};
     ld2.scratch = reinterpret_cast<const float2 *>(cb.scratch);
+    ld2.pf_dist = p.pf_dist;
     const bool lower = b.hi < (int64_t)C2::N / 2;
     if (fused_supported(p, LOGN) && cb.ctl) {
         return lower ? launch_fused<LOGN, true>(p, band_idx, b, s0, c0, nc, s, cb, ld1, st1, ld2, tw)
