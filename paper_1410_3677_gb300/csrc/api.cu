@@ -662,9 +662,10 @@ void parallel_for_threads(int nt, Fn f) {
     for (auto &x : th) x.join();
 }
 
-// Sorts the records by (cell, bin): a bucket pass over the cell range, then the
-// buckets sorted side by side.  rec and tmp hold n records; the result is in
-// the returned pointer (one of the two).
+// Sorts the records by (cell, bin): a bucket pass over the cell range into tmp,
+// then the buckets side by side, each by a counting sort over its cells back
+// into rec and a sort of each cell's records by bin.  rec and tmp hold n
+// records; the result is in the returned pointer (one of the two).
 fstat::CandRecord *sort_records(fstat::CandRecord *rec, fstat::CandRecord *tmp, int64_t n) {
     using fstat::CandRecord;
     auto less = [](const CandRecord &a, const CandRecord &b) { return cand_key(a) < cand_key(b); };
@@ -711,11 +712,49 @@ fstat::CandRecord *sort_records(fstat::CandRecord *rec, fstat::CandRecord *tmp, 
         int64_t *o = &off[(size_t)t * nb];
         for (int64_t i = a; i < b; ++i) tmp[o[bucket(rec[i])]++] = rec[i];
     });
+    // each bucket: counting sort by cell back into rec, then every cell's few
+    // records (tens at a typical threshold) by bin
     std::atomic<int> next{0};
     parallel_for_threads(nt, [&](int) {
-        for (int k; (k = next.fetch_add(1)) < nb;) std::sort(tmp + start[k], tmp + start[k + 1], less);
+        std::vector<int64_t> cnt;
+        for (int k; (k = next.fetch_add(1)) < nb;) {
+            const int64_t a = start[k], b = start[k + 1];
+            if (b - a < 64) {
+                std::copy(tmp + a, tmp + b, rec + a);
+                std::sort(rec + a, rec + b, less);
+                continue;
+            }
+            uint32_t cmin = UINT32_MAX, cmax = 0;
+            for (int64_t i = a; i < b; ++i) {
+                cmin = std::min(cmin, tmp[i].cell);
+                cmax = std::max(cmax, tmp[i].cell);
+            }
+            const size_t nc = (size_t)(cmax - cmin) + 1;
+            cnt.assign(nc + 1, 0);
+            for (int64_t i = a; i < b; ++i) ++cnt[tmp[i].cell - cmin + 1];
+            for (size_t c = 1; c <= nc; ++c) cnt[c] += cnt[c - 1];
+            for (int64_t i = a; i < b; ++i) rec[a + cnt[tmp[i].cell - cmin]++] = tmp[i];
+            // cnt[c] is now the end of cell c's run
+            int64_t lo_i = a;
+            for (size_t c = 0; c < nc; ++c) {
+                const int64_t hi_i = a + cnt[c];
+                if (hi_i - lo_i > 1) {
+                    if (hi_i - lo_i <= 32) {        // insertion sort by bin
+                        for (int64_t i = lo_i + 1; i < hi_i; ++i) {
+                            const CandRecord v = rec[i];
+                            int64_t j = i - 1;
+                            while (j >= lo_i && rec[j].bin > v.bin) { rec[j + 1] = rec[j]; --j; }
+                            rec[j + 1] = v;
+                        }
+                    } else {
+                        std::sort(rec + lo_i, rec + hi_i, less);
+                    }
+                }
+                lo_i = hi_i;
+            }
+        }
     });
-    return tmp;
+    return rec;
 }
 
 }  // namespace
