@@ -192,6 +192,17 @@ __device__ __forceinline__ void fill_twiddles(typename Vec2T<T>::type *tws, cons
 // One pass over a tile.  LD::load<R0, M/R0>(job, re, im) yields the elements
 // j + r M/R0 of sequence (t, f); ST::store<R, JPF>(job, re, im) receives outputs
 // j + r JPF (R = R1, JPF = R0 after two stages; R = M, JPF = 1 after one).
+// The CTA's dynamic shared memory (exchange area, then the twiddle table).
+__device__ __forceinline__ unsigned char *dyn_smem() {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    return smem_raw;
+}
+
+template <class LD, class = void>
+struct LoaderStaged { static constexpr bool value = false; };
+template <class LD>
+struct LoaderStaged<LD, decltype(void(LD::kStaged))> { static constexpr bool value = LD::kStaged; };
+
 // ZH: the stage-0 inputs r >= R0/2 (sequence elements >= M/2) are known to be
 // zero (the zero padding of a transform at least twice the series): the loader
 // is asked for R0/2 elements and the first DFT skips its zero half.
@@ -205,7 +216,7 @@ __device__ __forceinline__ void run_pass(LD &ld, ST &st, const T *__restrict__ t
     constexpr int JPF0 = M / R0, NJ0 = EH / R0;
     static_assert(EH % R0 == 0 && (R1 == 1 || EH % R1 == 0), "elements per thread vs radix");
     static_assert(MAPM != kMapW || (TPF <= 16 && 32 % TPF == 0), "warp mapping needs <= 16 threads per sequence");
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    unsigned char *smem_raw = dyn_smem();
     V *sd = reinterpret_cast<V *>(smem_raw);
     V *tws = reinterpret_cast<V *>(smem_raw + exch_bytes<T, M, SEQ>());
     fill_twiddles<T, M, THREADS>(tws, tw);
@@ -224,6 +235,9 @@ __device__ __forceinline__ void run_pass(LD &ld, ST &st, const T *__restrict__ t
 #pragma unroll
         for (int i = 0; i < NJ0; ++i) st.template store<R0, JPF0>(job<MAPM, SEQ, TPF, THREADS>(i), &re[i * R0], &im[i * R0]);
     } else {
+        // a loader that staged its input in the exchange area has been read out by
+        // every thread before the first scatter overwrites it
+        if constexpr (LoaderStaged<LD>::value) __syncthreads();
         // scatter: stage-0 output r of butterfly j goes to j R0 + r
 #pragma unroll
         for (int i = 0; i < NJ0; ++i) {

@@ -119,6 +119,7 @@ struct Plan {
     int fused_slots = kFusedSlots, fused_ahead = kFusedAhead;
     int fused_tpi = 4;             // tiles per ticket of the fused launch (power of two)
     int64_t pf_dist = 0;           // two-stage pass 2: L2 prefetch distance in CTAs (0: off)
+    bool tma = true;               // two-stage pass 2: rows staged by bulk copies
 
     // Bluestein / generic-FFT work buffers (double2)
     double *bw = nullptr;

@@ -156,6 +156,75 @@ struct ScratchLoad2 {
     }
 };
 
+// Pass 2 input staged by the TMA unit: the tile's rows are two contiguous runs
+// of F N1 complex floats (one per transform) in scratch; one thread copies both
+// into the CTA's exchange area with bulk copies completing on an mbarrier, and
+// the threads then read their butterflies' elements from shared memory (rows
+// unpadded there: a half-warp reads 16 consecutive elements, conflict-free).
+// The run_pass of a staged loader synchronises the CTA before the first scatter
+// overwrites the staged rows.
+template <class C>
+struct ScratchLoadTMA {
+    static constexpr bool kStaged = true;
+    const float2 *scratch;
+    int64_t pf_dist;        // see ScratchLoad2::prefetch_ahead
+    uint32_t *err;          // set when the copy does not complete within 1 s
+    const float2 *src;
+    const float2 *rows;     // staged rows in shared memory: [t F + f][N1]
+    uint64_t *bar;
+    __device__ void init(int tile, int64_t, int64_t slot) {
+        src = scratch + slot * 2 * C::N + (int64_t)tile * C::F * C::N1;
+        unsigned char *sm = eng2::dyn_smem();
+        rows = reinterpret_cast<const float2 *>(sm);
+        bar = reinterpret_cast<uint64_t *>(sm + C::SMEM);
+    }
+    __device__ void prefetch_ahead() const {
+        if (pf_dist <= 0 || threadIdx.x != 0) return;
+        const int64_t b = blockIdx.x + (int64_t)gridDim.x * blockIdx.y + pf_dist;
+        const int64_t total = (int64_t)gridDim.x * gridDim.y;
+        if (b >= total) return;
+        const int64_t slot = b / gridDim.x;
+        const int tile = (int)(b - slot * gridDim.x);
+        const float2 *r = scratch + slot * 2 * C::N + (int64_t)tile * C::F * C::N1;
+        constexpr uint32_t bytes = (uint32_t)(C::F * C::N1 * sizeof(float2));
+        ptx::bulk_prefetch_l2(r, bytes);
+        ptx::bulk_prefetch_l2(r + C::N, bytes);
+    }
+    // issue the copies (the whole CTA calls this once, before run_pass)
+    __device__ void stage() const {
+        constexpr uint32_t bytes = (uint32_t)(C::F * C::N1 * sizeof(float2));
+        static_assert(2 * bytes <= eng2::exch_bytes<float, C::M, C::SEQ>(), "staged rows fit the exchange area");
+        if (threadIdx.x == 0) {
+            ptx::mbar_init(bar, 1);
+            ptx::fence_mbar_init();
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            ptx::mbar_arrive_expect_tx(bar, 2 * bytes);
+            ptx::bulk_g2s(const_cast<float2 *>(rows), src, bytes, bar);
+            ptx::bulk_g2s(const_cast<float2 *>(rows) + C::F * C::N1, src + C::N, bytes, bar);
+        }
+    }
+    template <int R, int JPF>
+    __device__ __forceinline__ void load(const eng2::Job &q, float *re, float *im) const {
+        if (!ptx::mbar_try_wait(bar, 0)) {
+            const uint64_t t0 = ptx::globaltimer_ns();
+            bool late = false;
+            while (!ptx::mbar_try_wait(bar, 0)) {
+                const uint64_t dt = ptx::globaltimer_ns() - t0;
+                if (!late && dt > 1000000000ull) { atomicExch(err, 1u); late = true; }
+                if (dt > 2000000000ull) break;   // reported above; results are discarded
+            }
+        }
+        const float2 *row = rows + (q.t * C::F + q.f) * C::N1 + q.j;
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const float2 v = row[r * JPF];
+            re[r] = v.x; im[r] = v.y;
+        }
+    }
+};
+
 // Pass 2 output: F = |F_a|^2/(sigma^2 S_aa) + |F_b|^2/(sigma^2 S_bb) per bin
 // (Fig. 1, "F-statistics calculation"), strict 2F > thr, appended with one
 // atomic per warp and output slot.  Lanes l (F_a) and l ^ 16 (F_b) hold the same
@@ -236,6 +305,7 @@ __global__ void __launch_bounds__(256, 3) k_pass2(LD ld, ST st, const float *__r
     if constexpr (PASS == 2) ld.prefetch_ahead();
     ld.init(blockIdx.x, blockIdx.y, blockIdx.y);
     st.init(blockIdx.x, blockIdx.y, blockIdx.y);
+    if constexpr (eng2::LoaderStaged<LD>::value) ld.stage();
     eng2::run_pass<float, C::M, C::SEQ, C::EH, -1, MAPM, LD, ST, PASS == 1>(ld, st, tw);
 }
 
