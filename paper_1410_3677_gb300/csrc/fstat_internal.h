@@ -120,6 +120,7 @@ struct Plan {
     int fused_tpi = 4;             // tiles per ticket of the fused launch (power of two)
     int64_t pf_dist = 0;           // two-stage pass 2: L2 prefetch distance in CTAs (0: off)
     bool tma = true;               // two-stage pass 2: rows staged by bulk copies
+    int p2_threads = 128;          // two-stage pass 2 with bulk copies: CTA size 256 or 128
 
     // Bluestein / generic-FFT work buffers (double2)
     double *bw = nullptr;

@@ -15,7 +15,7 @@
 
 namespace fstat {
 
-template <int LOGN, int PASS>
+template <int LOGN, int PASS, int TS = 256>
 struct Cfg2 {
     static constexpr int LOGN1 = LOGN / 2;
     static constexpr int LOGN2 = LOGN - LOGN / 2;
@@ -26,13 +26,14 @@ struct Cfg2 {
     static constexpr int OTHER = PASS == 1 ? N1 : N2;    // number of such FFTs per transform
     static constexpr int EH = 32;
     static constexpr int TPF = M / EH;
-    static constexpr int SEQ0 = 256 / TPF;
+    static constexpr int SEQ0 = TS / TPF;
     static constexpr int SEQ = SEQ0 < 2 * OTHER ? SEQ0 : 2 * OTHER;   // sequences per tile
     static constexpr int F = SEQ / 2;                    // columns / rows per tile
     static constexpr int THREADS = SEQ * TPF;
     static constexpr int TILES = OTHER / F;
     static constexpr size_t SMEM = eng2::smem_bytes<float, M, SEQ>();
-    static_assert(M >= 64 && THREADS == 256, "tile shape");
+    static constexpr int MINB = 768 / TS;                // CTAs per SM (24 warps)
+    static_assert(M >= 64 && THREADS == TS, "tile shape");
 };
 
 // Pass 1 input: w[k] = (y a, y b) of one sky as float4, read as the float2 half
@@ -299,9 +300,9 @@ struct SearchEpi2 {
 // keeps no demodulation or twiddle-power state) and 3 x 68 KB of shared memory.
 // Pass 1 of a search transform (N_fft >= 2n) reads only the first half of each
 // column: elements k2 >= N2/2 lie at k >= N/2 >= n, in the zero padding.
-template <int LOGN, int PASS, int MAPM, class LD, class ST>
-__global__ void __launch_bounds__(256, 3) k_pass2(LD ld, ST st, const float *__restrict__ tw) {
-    using C = Cfg2<LOGN, PASS>;
+template <int LOGN, int PASS, int MAPM, class LD, class ST, int TS = 256>
+__global__ void __launch_bounds__(TS, 768 / TS) k_pass2(LD ld, ST st, const float *__restrict__ tw) {
+    using C = Cfg2<LOGN, PASS, TS>;
     if constexpr (PASS == 2) ld.prefetch_ahead();
     ld.init(blockIdx.x, blockIdx.y, blockIdx.y);
     st.init(blockIdx.x, blockIdx.y, blockIdx.y);

@@ -10,10 +10,10 @@
 namespace fstat {
 namespace {
 
-template <int LOGN, bool LOWER>
-SearchEpi2<Cfg2<LOGN, 2>, LOWER> make_epi(const Plan &p, int band_idx, const BandDev &b, int64_t c0,
-                                          int64_t s0, const CellBufs &cb) {
-    SearchEpi2<Cfg2<LOGN, 2>, LOWER> st2{};
+template <int LOGN, bool LOWER, int TS = 256>
+SearchEpi2<Cfg2<LOGN, 2, TS>, LOWER> make_epi(const Plan &p, int band_idx, const BandDev &b, int64_t c0,
+                                              int64_t s0, const CellBufs &cb) {
+    SearchEpi2<Cfg2<LOGN, 2, TS>, LOWER> st2{};
     st2.norm = cb.norm;
     st2.n_spin = (int)p.desc.n_spin;
     st2.c0 = c0;
@@ -28,12 +28,12 @@ SearchEpi2<Cfg2<LOGN, 2>, LOWER> make_epi(const Plan &p, int band_idx, const Ban
     return st2;
 }
 
-template <int LOGN, bool LOWER, class LD2>
+template <int LOGN, bool LOWER, int TS, class LD2>
 void launch_pass2(const Plan &p, int band_idx, const BandDev &b, int64_t s0, int64_t c0, int64_t nc,
                   cudaStream_t s, const CellBufs &cb, const LD2 &ld2, const TwiddleSet *tw, size_t extra) {
-    using C2 = Cfg2<LOGN, 2>;
-    const auto st2 = make_epi<LOGN, LOWER>(p, band_idx, b, c0, s0, cb);
-    auto k2 = k_pass2<LOGN, 2, eng2::kMapW, LD2, SearchEpi2<C2, LOWER>>;
+    using C2 = Cfg2<LOGN, 2, TS>;
+    const auto st2 = make_epi<LOGN, LOWER, TS>(p, band_idx, b, c0, s0, cb);
+    auto k2 = k_pass2<LOGN, 2, eng2::kMapW, LD2, SearchEpi2<C2, LOWER>, TS>;
     static bool attr2 = false;
     if (!attr2) { set_smem(k2, C2::SMEM + extra); attr2 = true; }
     k2<<<dim3(C2::TILES, (unsigned)nc), C2::THREADS, C2::SMEM + extra, s>>>(ld2, st2, tw->in1_f);
@@ -46,19 +46,27 @@ int launch_two(const Plan &p, int band_idx, const BandDev &b, int64_t s0, int64_
                const TwiddleSet *tw) {
     using C1 = Cfg2<LOGN, 1>;
     using C2 = Cfg2<LOGN, 2>;
-    auto k1 = k_pass2<LOGN, 1, eng2::kMapFJ, SearchLoad2<C1>, ScratchStore2<C1>>;
-    static bool attr1 = false;
-    if (!attr1) { set_smem(k1, C1::SMEM); attr1 = true; }
-    k1<<<dim3(C1::TILES, (unsigned)nc), C1::THREADS, C1::SMEM, s>>>(ld1, st1, tw->in2_f);
+    {
+        auto k1 = k_pass2<LOGN, 1, eng2::kMapFJ, SearchLoad2<C1>, ScratchStore2<C1>>;
+        static bool attr1 = false;
+        if (!attr1) { set_smem(k1, C1::SMEM); attr1 = true; }
+        k1<<<dim3(C1::TILES, (unsigned)nc), C1::THREADS, C1::SMEM, s>>>(ld1, st1, tw->in2_f);
+    }
     if (mid) cudaEventRecord(mid, s);
-    if (p.tma) {   // rows staged by bulk copies; an 8-byte mbarrier after the shared memory
+    if (p.tma && p.p2_threads == 128) {   // smaller tiles, six CTAs per SM
+        ScratchLoadTMA<Cfg2<LOGN, 2, 128>> lt{};
+        lt.scratch = ld2.scratch;
+        lt.pf_dist = 2 * ld2.pf_dist;
+        lt.err = p.qerr;
+        launch_pass2<LOGN, LOWER, 128>(p, band_idx, b, s0, c0, nc, s, cb, lt, tw, 16);
+    } else if (p.tma) {   // rows staged by bulk copies; an 8-byte mbarrier after the shared memory
         ScratchLoadTMA<C2> lt{};
         lt.scratch = ld2.scratch;
         lt.pf_dist = ld2.pf_dist;
         lt.err = p.qerr;
-        launch_pass2<LOGN, LOWER>(p, band_idx, b, s0, c0, nc, s, cb, lt, tw, 16);
+        launch_pass2<LOGN, LOWER, 256>(p, band_idx, b, s0, c0, nc, s, cb, lt, tw, 16);
     } else {
-        launch_pass2<LOGN, LOWER>(p, band_idx, b, s0, c0, nc, s, cb, ld2, tw, 0);
+        launch_pass2<LOGN, LOWER, 256>(p, band_idx, b, s0, c0, nc, s, cb, ld2, tw, 0);
     }
     return 2;
 }

@@ -57,6 +57,9 @@ FUSED = {"FSTAT_PERSISTENT": "0", "FSTAT_FUSED": "1"}    # two-stage engine, one
     (TWO, {"FSTAT_FUSED": "0", "FSTAT_CELL_BATCH": "1", "FSTAT_STREAMS": "3"}),
     (TWO, DEFAULT),
     (TWO, {"FSTAT_CELL_BATCH": "2"}),
+    (TWO, {"FSTAT_TMA": "0"}),
+    (TWO, {"FSTAT_P2_THREADS": "256"}),
+    (TWO, {"FSTAT_PF_DIST": "0", "FSTAT_CELL_BATCH": "9"}),
     (TWO, {"FSTAT_CELL_BATCH": "5", "FSTAT_STREAMS": "2"}),
     (TWO, FUSED),
     (TWO, {"FSTAT_FUSED": "1", "FSTAT_CELL_BATCH": "3"}),
