@@ -333,6 +333,7 @@ void create_impl(Plan &p, const fstat_plan_desc *d) {
     // a worker's slot holds a launch's cells, or the ring of the fused launch
     if (fp32) {
         if (const char *v = getenv("FSTAT_FUSED")) p.fused = atoi(v) != 0;
+        if (const char *v = getenv("FSTAT_GRAPH")) p.use_graph = atoi(v) != 0;
         {   // pass-2 prefetch distance: one CTA per resident slot (3 per SM) ahead
             int dev = 0, sms = 0;
             check(cudaGetDevice(&dev), "cudaGetDevice");
@@ -404,6 +405,8 @@ void create_impl(Plan &p, const fstat_plan_desc *d) {
 }
 
 void free_all(Plan &p) {
+    if (p.graph.exec) cudaGraphExecDestroy(p.graph.exec);
+    p.graph.exec = nullptr;
     if (!p.allocs.empty() || p.own_stream) cudaDeviceSynchronize();
     for (void *ptr : p.allocs) cudaFree(ptr);
     p.allocs.clear();
@@ -429,6 +432,8 @@ int stat_index(Plan &p, const char *name) {
     return (int)p.kstats.size() - 1;
 }
 
+void rec_timing(cudaEvent_t e, cudaStream_t s) { check(record_timing_event(e, s), "event"); }
+
 cudaEvent_t ev_get(Plan &p) {
     if (!p.ev_pool.empty()) {
         cudaEvent_t e = p.ev_pool.back();
@@ -451,7 +456,7 @@ bool stat_launch(Plan &p, int idx, double flops, double bytes) {
     return p.timing_every > 0 && (k.launches - 1) % p.timing_every == 0;
 }
 
-void collect_timing(Plan &p) {
+void collect_timing(Plan &p, bool recycle = true) {
     std::vector<cudaEvent_t> used;
     for (auto &pe : p.pending) {
         float ms = 0.f;
@@ -464,7 +469,8 @@ void collect_timing(Plan &p) {
     // an event may close one interval and open the next: return each once
     std::sort(used.begin(), used.end());
     used.erase(std::unique(used.begin(), used.end()), used.end());
-    for (cudaEvent_t e : used) p.ev_pool.push_back(e);
+    if (recycle)
+        for (cudaEvent_t e : used) p.ev_pool.push_back(e);
     p.pending.clear();
 }
 
@@ -474,13 +480,13 @@ void band_prologue(Plan &p, BandDev &b) {
     const int idx = stat_index(p, "band_prologue");
     const bool t = stat_launch(p, idx, 0.0, (double)b.n * 8.0 * (1 + p.desc.upsample));
     cudaEvent_t e0 = nullptr, e1 = nullptr;
-    if (t) { e0 = ev_get(p); e1 = ev_get(p); check(cudaEventRecord(e0, p.stream), "event"); }
+    if (t) { e0 = ev_get(p); e1 = ev_get(p); rec_timing(e0, p.stream); }
     p.launches += launch_sigma2(b.x, b.n, p.desc.sigma2, p.partials, b.sigma2, p.stream);
     p.launches += launch_upsample(p, b, p.desc.upsample, b.xu, fp32, p.stream);
-    if (t) { check(cudaEventRecord(e1, p.stream), "event"); p.pending.push_back({idx, e0, e1}); }
+    if (t) { rec_timing(e1, p.stream); p.pending.push_back({idx, e0, e1}); }
 }
 
-void search_impl(Plan &p, int64_t begin, int64_t end) {
+void enqueue_search(Plan &p, int64_t begin, int64_t end) {
     const fstat_plan_desc &d = p.desc;
     const bool fp32 = d.form == FSTAT_FP32_BATCHED;
     cudaStream_t s = p.stream;
@@ -534,10 +540,10 @@ void search_impl(Plan &p, int64_t begin, int64_t end) {
             const bool tg = stat_launch(p, i_geo, 0.0,
                                         (double)b.n * (24.0 + welem * ns) + (double)p.desc.upsample * b.n * (fp32 ? 4 : 8));
             cudaEvent_t g0 = nullptr, g1 = nullptr;
-            if (tg) { g0 = ev_get(p); g1 = ev_get(p); check(cudaEventRecord(g0, s), "event"); }
+            if (tg) { g0 = ev_get(p); g1 = ev_get(p); rec_timing(g0, s); }
             p.launches += launch_geometry(p, b, sb, ns, fp32, p.wbuf[par], nullptr, nullptr, nullptr, nullptr, s);
             p.launches += launch_reduce_norms(p, b, ns, p.normbuf[par], s);
-            if (tg) { check(cudaEventRecord(g1, s), "event"); p.pending.push_back({i_geo, g0, g1}); }
+            if (tg) { rec_timing(g1, s); p.pending.push_back({i_geo, g0, g1}); }
             const int64_t c_lo = std::max<int64_t>(lc0, sb * d.n_spin);
             const int64_t c_hi = std::min<int64_t>(lc1, (sb + ns) * d.n_spin);
             if (fp32 && p.use_persistent && persistent_supported(b.logn)) {
@@ -545,10 +551,10 @@ void search_impl(Plan &p, int64_t begin, int64_t end) {
                 const bool tp = stat_launch(p, i_pp, 2.0 * (c_hi - c_lo) * 5.0 * nfft * (lg1 + lg2),
                                             (double)ns * b.n * welem);
                 cudaEvent_t e0 = nullptr, e1 = nullptr;
-                if (tp) { e0 = ev_get(p); e1 = ev_get(p); check(cudaEventRecord(e0, s), "event"); }
+                if (tp) { e0 = ev_get(p); e1 = ev_get(p); rec_timing(e0, s); }
                 const CellBufs cbuf{p.wbuf[par], p.normbuf[par], p.scratch};
                 p.launches += launch_search_persistent(p, bi, b, sb, c_lo, c_hi, s, cbuf);
-                if (tp) { check(cudaEventRecord(e1, s), "event"); p.pending.push_back({i_pp, e0, e1}); }
+                if (tp) { rec_timing(e1, s); p.pending.push_back({i_pp, e0, e1}); }
                 if (NW > 1)
                     for (int i = 0; i < NW; ++i) check(cudaEventRecord(p.ev_done[par][i], s), "event");
                 continue;
@@ -572,11 +578,11 @@ void search_impl(Plan &p, int64_t begin, int64_t end) {
                     const bool tf = stat_launch(p, i_fu, 2.0 * nc * 5.0 * nfft * (lg1 + lg2),
                                                 (double)(sky_b - sky_a + 1) * b.n * welem);
                     cudaEvent_t e0 = nullptr, e1 = nullptr;
-                    if (tf) { e0 = ev_get(p); e1 = ev_get(p); check(cudaEventRecord(e0, ws), "event"); }
+                    if (tf) { e0 = ev_get(p); e1 = ev_get(p); rec_timing(e0, ws); }
                     const int L = launch_search_cells_f32(p, bi, b, sb, c, nc, ws, nullptr, cbuf);
                     if (L < 0) throw std::string("unsupported transform length");
                     p.launches += L;
-                    if (tf) { check(cudaEventRecord(e1, ws), "event"); p.pending.push_back({i_fu, e0, e1}); }
+                    if (tf) { rec_timing(e1, ws); p.pending.push_back({i_fu, e0, e1}); }
                     continue;
                 }
                 // 5 N log2 N per complex transform, split between the passes; two
@@ -588,14 +594,14 @@ void search_impl(Plan &p, int64_t begin, int64_t end) {
                 cudaEvent_t e0 = nullptr, e1 = nullptr, e2 = nullptr;
                 if (t1) {
                     e0 = ev_get(p); e1 = ev_get(p); e2 = ev_get(p);
-                    check(cudaEventRecord(e0, ws), "event");
+                    rec_timing(e0, ws);
                 }
                 const int L = fp32 ? launch_search_cells_f32(p, bi, b, sb, c, nc, ws, e1, cbuf)
                                    : launch_search_cells_f64(p, bi, b, sb, c, nc, ws, e1, cbuf);
                 if (L < 0) throw std::string("unsupported transform length");
                 p.launches += L;
                 if (t1) {
-                    check(cudaEventRecord(e2, ws), "event");
+                    rec_timing(e2, ws);
                     p.pending.push_back({i_p1, e0, e1});
                     p.pending.push_back({i_p2, e1, e2});
                 }
@@ -606,8 +612,12 @@ void search_impl(Plan &p, int64_t begin, int64_t end) {
     }
     join_workers();
     check(cudaGetLastError(), "search launch");
-    check(cudaStreamSynchronize(s), "search");
-    collect_timing(p);
+}
+
+// Waits for the search, reads the error word and the candidate count.
+void finish_search(Plan &p, bool recycle_events) {
+    check(cudaStreamSynchronize(p.stream), "search");
+    collect_timing(p, recycle_events);
     if (p.qerr) {
         uint32_t e = 0;
         check(cudaMemcpy(&e, p.qerr, sizeof(e), cudaMemcpyDeviceToHost), "queue status");
@@ -617,6 +627,77 @@ void search_impl(Plan &p, int64_t begin, int64_t end) {
     check(cudaMemcpy(&cnt, p.cand_count, sizeof(cnt), cudaMemcpyDeviceToHost), "count");
     p.last_total = (int64_t)cnt;
     p.searched = true;
+}
+
+void drop_graph(Plan &p) {
+    if (p.graph.exec) cudaGraphExecDestroy(p.graph.exec);
+    // its events go back to the pool
+    for (auto &pe : p.graph.pending) { p.ev_pool.push_back(pe.a); p.ev_pool.push_back(pe.b); }
+    std::sort(p.ev_pool.begin(), p.ev_pool.end());
+    p.ev_pool.erase(std::unique(p.ev_pool.begin(), p.ev_pool.end()), p.ev_pool.end());
+    p.graph = Plan::GraphRun{};
+}
+
+// One search: the launch sequence is captured into a CUDA graph the first time
+// a cell range is searched (at the current timing rate) and replayed after
+// that, so a repeated search costs one graph launch on the host.
+void search_impl(Plan &p, int64_t begin, int64_t end) {
+    auto &g = p.graph;
+    const bool hit = g.exec && g.begin == begin && g.end == end && g.timing_every == p.timing_every;
+    // capture only a search that repeats the previous one (a plan searched once
+    // never pays for the capture)
+    const bool repeat = p.prev_begin == begin && p.prev_end == end && p.prev_timing == p.timing_every;
+    p.prev_begin = begin;
+    p.prev_end = end;
+    p.prev_timing = p.timing_every;
+    if (!p.use_graph || (!hit && !repeat)) {
+        enqueue_search(p, begin, end);
+        finish_search(p, true);
+        return;
+    }
+    if (!hit) {
+        drop_graph(p);
+        const std::vector<Plan::KStat> before = p.kstats;
+        const int64_t launches0 = p.launches;
+        cudaGraph_t graph = nullptr;
+        check(cudaStreamBeginCapture(p.stream, cudaStreamCaptureModeThreadLocal), "graph capture");
+        try {
+            enqueue_search(p, begin, end);
+        } catch (...) {
+            cudaStreamEndCapture(p.stream, &graph);
+            if (graph) cudaGraphDestroy(graph);
+            throw;
+        }
+        check(cudaStreamEndCapture(p.stream, &graph), "graph capture");
+        const cudaError_t ie = cudaGraphInstantiate(&g.exec, graph, 0);
+        cudaGraphDestroy(graph);
+        check(ie, "graph instantiate");
+        g.begin = begin;
+        g.end = end;
+        g.timing_every = p.timing_every;
+        g.launches = p.launches - launches0;
+        g.dk = p.kstats;
+        for (size_t i = 0; i < g.dk.size(); ++i) {
+            const Plan::KStat b0 = i < before.size() ? before[i] : Plan::KStat{};
+            g.dk[i].launches -= b0.launches;
+            g.dk[i].flops -= b0.flops;
+            g.dk[i].bytes -= b0.bytes;
+        }
+        g.pending = p.pending;   // the capture's host counters stand for this first run
+    } else {
+        for (const auto &k : g.dk) {   // by name: the statistics may have been reset since
+            if (k.launches == 0) continue;
+            auto &t = p.kstats[(size_t)stat_index(p, k.name.c_str())];
+            t.launches += k.launches;
+            t.flops += k.flops;
+            t.bytes += k.bytes;
+        }
+        p.launches += g.launches;
+        p.pending = g.pending;
+        for (auto &pe : p.pending) pe.stat = stat_index(p, g.dk[(size_t)pe.stat].name.c_str());
+    }
+    check(cudaGraphLaunch(g.exec, p.stream), "graph launch");
+    finish_search(p, false);
 }
 
 template <class F>

@@ -153,6 +153,21 @@ struct Plan {
     std::vector<Pending> pending;
     std::vector<cudaEvent_t> ev_pool, ev_all;
 
+    // CUDA graph of the last search's launch sequence, replayed while the cell
+    // range and the timing rate stay the same; with it the host-side counters
+    // and the timing events its replay produces
+    bool use_graph = true;
+    int64_t prev_begin = -1, prev_end = -1;
+    int prev_timing = -1;
+    struct GraphRun {
+        cudaGraphExec_t exec = nullptr;
+        int64_t begin = -1, end = -1;
+        int timing_every = 0;
+        int64_t launches = 0;                    // kernels per replay
+        std::vector<KStat> dk;                   // counter increments per replay
+        std::vector<Pending> pending;            // events recorded by the graph (owned by it)
+    } graph;
+
     const TwiddleSet *twiddles(int logn) const {
         for (auto &t : tw)
             if (t.logn == logn) return &t;
@@ -210,6 +225,15 @@ int persistent_tiles_per_cell(int logn);
 int launch_search_persistent(const Plan &p, int band_idx, const BandDev &b, int64_t s0,
                              int64_t c_lo, int64_t c_hi, cudaStream_t s, const CellBufs &cb);
 
+// Records a timing event on s, as an external event node while s is being
+// captured into a graph (so that the event stays readable after replays).
+inline cudaError_t record_timing_event(cudaEvent_t e, cudaStream_t s) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    const cudaError_t r = cudaStreamIsCapturing(s, &cs);
+    if (r != cudaSuccess) return r;
+    return cudaEventRecordWithFlags(e, s, cs == cudaStreamCaptureStatusActive ? cudaEventRecordExternal
+                                                                               : cudaEventRecordDefault);
+}
 // Whether the FP32 cells of a band of length 2^logn run as one fused launch.
 bool fused_supported(const Plan &p, int logn);
 // `mid` (may be null) is recorded between the two passes.

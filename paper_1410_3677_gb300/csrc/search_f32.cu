@@ -52,7 +52,7 @@ int launch_two(const Plan &p, int band_idx, const BandDev &b, int64_t s0, int64_
         if (!attr1) { set_smem(k1, C1::SMEM); attr1 = true; }
         k1<<<dim3(C1::TILES, (unsigned)nc), C1::THREADS, C1::SMEM, s>>>(ld1, st1, tw->in2_f);
     }
-    if (mid) cudaEventRecord(mid, s);
+    if (mid) record_timing_event(mid, s);
     if (p.tma && p.p2_threads == 128) {   // smaller tiles, six CTAs per SM
         ScratchLoadTMA<Cfg2<LOGN, 2, 128>> lt{};
         lt.scratch = ld2.scratch;

@@ -44,7 +44,7 @@ int launch_search_t(const Plan &p, int band_idx, const BandDev &b, int64_t s0, i
     static bool attr1 = false;
     if (!attr1) { set_smem(k1, C1::SMEM); attr1 = true; }
     k1<<<dim3(C1::TILES, (unsigned)nc), C1::THREADS, C1::SMEM, s>>>(ld1, st1, tin2);
-    if (mid) cudaEventRecord(mid, s);
+    if (mid) record_timing_event(mid, s);
 
     using LD2 = ScratchLoad<T, C2>;
     using ST2 = SearchEpi<T, C2>;

@@ -45,6 +45,15 @@ def test_library_exports_every_declared_symbol(fs):
         assert hasattr(fs._lib, name)
 
 
+def test_library_leaves_no_internal_symbol_unresolved(fs):
+    """Every function of the library's own namespace is defined in it (a missing
+    definition would only show at the first call)."""
+    out = subprocess.run(["nm", "-D", "--undefined-only", fs.LIB_PATH], capture_output=True,
+                         text=True, check=True).stdout
+    missing = [ln.split()[-1] for ln in out.splitlines() if "_ZN5fstat" in ln]
+    assert not missing, missing
+
+
 def test_struct_layouts(fs):
     assert C.sizeof(fs.fstat_band) == 72
     assert C.sizeof(fs.fstat_candidate) == 72

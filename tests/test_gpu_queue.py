@@ -143,3 +143,45 @@ def test_fused_launch_withheld_completion_times_out(fs):
     p, rc, c, total = _run(fs, w, 20.0)
     p.close()
     assert rc == fs.FSTAT_OK and total > 0
+
+
+def test_graph_replay_repeats_the_search(fs):
+    """A search repeated over the same cell range is captured into a CUDA graph
+    on its second run and replayed after that: identical candidates, the same
+    kernel count per search, and a recapture when the range changes."""
+    w = S.workload(3, n_sky=70, n_spin=8)
+    p = fs.Plan(w.bands, w.alpha, w.delta, w.fdot, 25.0, lat=w.lat, gamma=w.gamma,
+                upsample=w.upsample, form=fs.FP32_BATCHED, cand_capacity=1 << 22)
+    p.set_timing(2)
+    ref = None
+    launches = []
+    for rng in [(0, -1)] * 4 + [(8, 300)] * 3 + [(0, -1)] * 3:
+        k0 = p.info()["kernel_launches"]
+        assert p.search(*rng) == fs.FSTAT_OK
+        launches.append((rng, p.info()["kernel_launches"] - k0))
+        c, total = p.candidates()
+        if rng == (0, -1):
+            if ref is None:
+                ref = c
+            assert np.array_equal(c, ref)
+        else:
+            cell = c["sky"] * w.n_spin + c["spin"]
+            assert np.all((cell >= 8) & (cell < 300))
+            sel = ref[(ref["sky"] * w.n_spin + ref["spin"] >= 8) & (ref["sky"] * w.n_spin + ref["spin"] < 300)]
+            assert np.array_equal(c, sel)
+    full = {n for r, n in launches if r == (0, -1)}
+    part = {n for r, n in launches if r == (8, 300)}
+    assert len(full) == 1 and len(part) == 1
+    stats = p.kernel_stats()
+    assert any(v["timed_launches"] > 0 for v in stats.values())
+    p.close()
+    os.environ["FSTAT_GRAPH"] = "0"
+    try:
+        q = fs.Plan(w.bands, w.alpha, w.delta, w.fdot, 25.0, lat=w.lat, gamma=w.gamma,
+                    upsample=w.upsample, form=fs.FP32_BATCHED, cand_capacity=1 << 22)
+    finally:
+        del os.environ["FSTAT_GRAPH"]
+    for _ in range(3):
+        q.search()
+        assert np.array_equal(q.candidates()[0], ref)
+    q.close()
