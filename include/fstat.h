@@ -179,6 +179,30 @@ fstat_status fstat_plan_set_timing(fstat_plan *plan, int sample_every);
 fstat_status fstat_plan_kernel_stats(const fstat_plan *plan, fstat_kernel_stat *out, int cap,
                                      int *n);
 
+/* Launch-shape autotuner of an FSTAT_FP32_BATCHED plan (the paper's farm has no
+   counterpart; it picks the GPU-side shapes the search runs with).  It times
+   whole searches over the cells [0, sample_cells) (clamped to the grid) with
+   CUDA events, changing one choice at a time -- FFT engine (two-stage radix
+   32x16 / radix-8 Stockham), pass-2 tile (128 or 256 threads) and loader (bulk
+   copies or per-thread loads with L2 prefetch), cells per launch pair, one fused
+   ticket-ordered launch or two launches -- keeps a change only when it is at
+   least 1 % faster, and leaves the plan configured with the best found.  The
+   candidates of the tuning searches are discarded (fstat_candidates_get then
+   reports none until the next fstat_search).  *chosen (may be NULL) receives the
+   configuration and the measured milliseconds per sampled cell.  Results never
+   depend on the choice beyond FP32 rounding (every shape computes the same
+   transforms).  FSTAT_ERR_ARG for an FP64_PLAIN plan or sample_cells < 1. */
+typedef struct {
+    int32_t engine;          /* 2: two-stage engine, 1: radix-8 engine */
+    int32_t pass2_threads;   /* 128 or 256 */
+    int32_t pass2_bulk_copy; /* 1: bulk-copy staging, 0: per-thread loads */
+    int32_t fused;           /* 1: one ticket-ordered launch per batch */
+    int64_t cells_per_launch;
+    double ms_per_cell;      /* of the chosen configuration on the sample */
+} fstat_tuning;
+
+fstat_status fstat_plan_autotune(fstat_plan *plan, int64_t sample_cells, fstat_tuning *chosen);
+
 /* Allocation-free F of one cell (the paper has no counterpart: this entry point
    exists for callers that cannot allocate device memory -- for example a host
    application that reserves the whole device memory budget up front and hands

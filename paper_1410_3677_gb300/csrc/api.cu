@@ -978,6 +978,74 @@ fstat_status fstat_debug_sky(fstat_plan *p, int band, int64_t sky, double *y, do
     });
 }
 
+fstat_status fstat_plan_autotune(fstat_plan *p, int64_t sample_cells, fstat_tuning *chosen) {
+    return guarded(p, [&]() -> fstat_status {
+        if (p->desc.form != FSTAT_FP32_BATCHED || sample_cells < 1) {
+            p->err = "autotune needs an FP32_BATCHED plan and sample_cells >= 1";
+            return FSTAT_ERR_ARG;
+        }
+        const int64_t nc = std::min<int64_t>(sample_cells, p->n_cells);
+        const int timing = p->timing_every;
+        const bool graph = p->use_graph;
+        p->timing_every = 0;
+        p->use_graph = false;
+        drop_graph(*p);
+        cudaEvent_t e0 = ev_get(*p), e1 = ev_get(*p);
+        auto time_once = [&]() -> double {
+            check(cudaEventRecord(e0, p->stream), "event");
+            enqueue_search(*p, 0, nc);
+            check(cudaEventRecord(e1, p->stream), "event");
+            finish_search(*p, true);
+            float ms = 0.f;
+            check(cudaEventElapsedTime(&ms, e0, e1), "cudaEventElapsedTime");
+            return ms;
+        };
+        auto measure = [&]() -> double {   // best of two after one untimed run
+            time_once();
+            return std::min(time_once(), time_once());
+        };
+        double best = measure();
+        // one choice at a time; a change stays when it is >= 1 % faster
+        auto try_set = [&](auto set, auto undo) {
+            set();
+            const double t = measure();
+            if (t < 0.99 * best) best = t;
+            else undo();
+        };
+        const int64_t cb0 = p->cell_batch;
+        for (int64_t cb : {int64_t(256), int64_t(512)}) {
+            if (cb >= p->cell_batch) continue;
+            const int64_t old = p->cell_batch;
+            try_set([&] { p->cell_batch = cb; }, [&] { p->cell_batch = old; });
+        }
+        (void)cb0;
+        { const int old = p->p2_threads;
+          try_set([&] { p->p2_threads = old == 128 ? 256 : 128; }, [&] { p->p2_threads = old; }); }
+        { const bool old = p->tma;
+          try_set([&] { p->tma = !old; }, [&] { p->tma = old; }); }
+        { const bool old = p->fused;
+          try_set([&] { p->fused = !old; }, [&] { p->fused = old; }); }
+        { const int old = p->engine;
+          try_set([&] { p->engine = old == 2 ? 1 : 2; }, [&] { p->engine = old; }); }
+        p->ev_pool.push_back(e0);
+        p->ev_pool.push_back(e1);
+        p->timing_every = timing;
+        p->use_graph = graph;
+        p->kstats.clear();
+        p->searched = false;
+        p->prev_begin = p->prev_end = -1;
+        if (chosen) {
+            chosen->engine = p->engine;
+            chosen->pass2_threads = p->p2_threads;
+            chosen->pass2_bulk_copy = p->tma ? 1 : 0;
+            chosen->fused = p->fused ? 1 : 0;
+            chosen->cells_per_launch = p->cell_batch;
+            chosen->ms_per_cell = best / (double)nc;
+        }
+        return FSTAT_OK;
+    });
+}
+
 fstat_status fstat_plan_set_timing(fstat_plan *p, int sample_every) {
     return guarded(p, [&]() -> fstat_status {
         if (sample_every < 0) { p->err = "sample_every must be >= 0"; return FSTAT_ERR_ARG; }

@@ -53,6 +53,11 @@ class fstat_kernel_stat(C.Structure):
                 ("timed_ms", f64), ("flops_per_launch", f64), ("bytes_per_launch", f64)]
 
 
+class fstat_tuning(C.Structure):
+    _fields_ = [("engine", i32), ("pass2_threads", i32), ("pass2_bulk_copy", i32), ("fused", i32),
+                ("cells_per_launch", i64), ("ms_per_cell", f64)]
+
+
 class fstat_plan_info(C.Structure):
     _fields_ = [("n_cells", i64), ("f_evals", i64), ("device_bytes", i64),
                 ("kernel_launches", i64), ("n_fft_max", i64)]
@@ -79,6 +84,8 @@ _lib.fstat_plan_set_timing.argtypes = [_plan_p, i32]
 _lib.fstat_plan_set_timing.restype = i32
 _lib.fstat_plan_kernel_stats.argtypes = [_plan_p, P(fstat_kernel_stat), i32, P(i32)]
 _lib.fstat_plan_kernel_stats.restype = i32
+_lib.fstat_plan_autotune.argtypes = [_plan_p, i64, P(fstat_tuning)]
+_lib.fstat_plan_autotune.restype = i32
 _lib.fstat_cell_F_noalloc.argtypes = [C.c_void_p, i64, i64, f64, f64, f64, i64, i64,
                                        C.c_void_p, C.c_void_p]
 _lib.fstat_cell_F_noalloc.restype = i32
@@ -91,6 +98,7 @@ _lib.fstat_plan_error.restype = C.c_char_p
 
 EXPORTED = ["fstat_plan_create", "fstat_search", "fstat_candidates_get", "fstat_debug_sky",
             "fstat_plan_get_info", "fstat_plan_set_timing", "fstat_plan_kernel_stats",
+            "fstat_plan_autotune",
             "fstat_cell_F_noalloc", "fstat_plan_destroy", "fstat_status_string",
             "fstat_plan_error"]
 
@@ -226,6 +234,15 @@ class Plan:
         inf = fstat_plan_info()
         _lib.fstat_plan_get_info(self._h, C.byref(inf))
         return {k: getattr(inf, k) for k, _ in fstat_plan_info._fields_}
+
+    def autotune(self, sample_cells: int):
+        """Pick the launch shapes by timing searches over the first sample_cells
+        cells; returns the chosen configuration."""
+        t = fstat_tuning()
+        rc = _lib.fstat_plan_autotune(self._h, int(sample_cells), C.byref(t))
+        if rc != FSTAT_OK:
+            self._raise(rc, "fstat_plan_autotune")
+        return {k: getattr(t, k) for k, _ in fstat_tuning._fields_}
 
     def set_timing(self, sample_every: int):
         rc = _lib.fstat_plan_set_timing(self._h, int(sample_every))

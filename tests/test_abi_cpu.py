@@ -59,6 +59,7 @@ def test_struct_layouts(fs):
     assert C.sizeof(fs.fstat_candidate) == 72
     assert C.sizeof(fs.fstat_plan_desc) == 144
     assert C.sizeof(fs.fstat_plan_info) == 40
+    assert C.sizeof(fs.fstat_tuning) == 32
 
 
 def test_status_strings(fs):

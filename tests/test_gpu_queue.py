@@ -185,3 +185,32 @@ def test_graph_replay_repeats_the_search(fs):
         q.search()
         assert np.array_equal(q.candidates()[0], ref)
     q.close()
+
+
+def test_autotune_keeps_results(fs):
+    """The autotuner times searches over a sample of cells and leaves the plan on
+    its best launch shapes; the candidates stay within FP32 rounding of the
+    default shapes' (exactly equal for the shapes that share the engine)."""
+    w = S.workload(3, n_sky=40, n_spin=8)
+    def plan():
+        return fs.Plan(w.bands, w.alpha, w.delta, w.fdot, 25.0, lat=w.lat, gamma=w.gamma,
+                       upsample=w.upsample, form=fs.FP32_BATCHED, cand_capacity=1 << 22)
+    p0 = plan()
+    p0.search()
+    ref, _ = p0.candidates()
+    p0.close()
+    p = plan()
+    t = p.autotune(64)
+    assert t["engine"] in (1, 2) and t["pass2_threads"] in (128, 256)
+    assert t["cells_per_launch"] >= 1 and t["ms_per_cell"] > 0
+    assert p.candidates()[1] == 0                      # tuning searches are discarded
+    p.search()
+    c, _ = p.candidates()
+    p.close()
+    if t["engine"] == 2:
+        assert np.array_equal(c, ref)
+    else:
+        keys = ("sky", "spin", "bin")
+        common = {tuple(x) for x in np.stack([ref[k] for k in keys], 1).tolist()} & \
+                 {tuple(x) for x in np.stack([c[k] for k in keys], 1).tolist()}
+        assert len(common) >= 0.99 * min(len(ref), len(c))
