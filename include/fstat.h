@@ -80,6 +80,15 @@ typedef struct {
                             else a power of two >= 2n, 256 <= n_fft <= 2^20 */
 } fstat_band;
 
+/* The statistic evaluated per bin.  FSTAT_F_SIMPLE: F = |F_a|^2/(sigma^2 S_aa) +
+   |F_b|^2/(sigma^2 S_bb) (the amplitude cross term S_ab neglected).  FSTAT_F_FULL:
+   the Jaranowski-Krolak-Schutz form
+     F = (S_bb |F_a|^2 + S_aa |F_b|^2 - 2 S_ab Re(F_a conj(F_b))) / (sigma^2 D),
+     D = S_aa S_bb - S_ab^2,
+   whose 2F follows a chi-square law with 4 degrees of freedom in Gaussian noise.
+   S_aa, S_bb, S_ab are the sums of a^2, b^2, a b over the resampled window. */
+typedef enum { FSTAT_F_SIMPLE = 0, FSTAT_F_FULL = 1 } fstat_statistic;
+
 typedef struct {
     int n_bands;                 /* >= 1 */
     const fstat_band *bands;     /* [n_bands] */
@@ -95,6 +104,7 @@ typedef struct {
     double gamma;                /* arm-bisector orientation, counter-clockwise from
                                     local East, rad */
     int upsample;                /* U of the FFT upsample, 1..8 (2 recommended) */
+    int statistic;               /* FSTAT_F_SIMPLE (0) or FSTAT_F_FULL (1), see below */
     double sigma2;               /* noise variance; <= 0: (1/N) sum x^2 per band */
     fstat_form form;
     int64_t cand_capacity;       /* device candidate records kept per search, >= 1 */

@@ -113,6 +113,7 @@ fstat_status validate(const fstat_plan_desc *d, std::string &err) {
     if (d->n_sky < 1 || !d->alpha || !d->delta) { err = "need n_sky >= 1, alpha, delta"; return FSTAT_ERR_ARG; }
     if (d->n_spin < 1 || !d->fdot) { err = "need n_spin >= 1 and fdot"; return FSTAT_ERR_ARG; }
     if (d->form != FSTAT_FP64_PLAIN && d->form != FSTAT_FP32_BATCHED) { err = "unknown form"; return FSTAT_ERR_ARG; }
+    if (d->statistic != FSTAT_F_SIMPLE && d->statistic != FSTAT_F_FULL) { err = "unknown statistic"; return FSTAT_ERR_ARG; }
     if (d->upsample < 1 || d->upsample > 8) { err = "upsample must be 1..8"; return FSTAT_ERR_ARG; }
     if (d->cand_capacity < 1 || d->cand_capacity > (int64_t(1) << 34)) { err = "cand_capacity out of range"; return FSTAT_ERR_ARG; }
     if (!is_finite(d->thr_2F) || !is_finite(d->lat) || !is_finite(d->gamma) || !is_finite(d->sigma2)) {
@@ -311,7 +312,7 @@ void create_impl(Plan &p, const fstat_plan_desc *d) {
     p.dbuf = dalloc<double>(p, (size_t)p.sky_batch * p.n_max, n_alloc);
     p.partials = dalloc<double>(p, std::max<int64_t>((int64_t)p.sky_batch * nblk * 3, 256), n_alloc);
     p.S = dalloc<double>(p, 3 * p.sky_batch, n_alloc);
-    for (int q = 0; q < 2; ++q) p.normbuf[q] = dalloc<double>(p, 2 * p.sky_batch, n_alloc);
+    for (int q = 0; q < 2; ++q) p.normbuf[q] = dalloc<double>(p, 4 * p.sky_batch, n_alloc);
 
     // FFT scratch: cell slots of 2 transforms; also hosts the generic FFT of the upsample
     const size_t tsz = fp32 ? sizeof(float2) : sizeof(double2);

@@ -267,7 +267,7 @@ __global__ void __launch_bounds__(256) k_geometry(GeoArgs g) {
 // 1/(sigma^2 S_aa), 1/(sigma^2 S_bb).
 __global__ void k_reduce_norms(const double *__restrict__ partials, int nblk,
                                const double *__restrict__ sigma2, double *__restrict__ S,
-                               double *__restrict__ norm) {
+                               double *__restrict__ norm, int full) {
     const int sl = blockIdx.x;
     double out[3];
 #pragma unroll
@@ -281,8 +281,23 @@ __global__ void k_reduce_norms(const double *__restrict__ partials, int nblk,
         S[3 * sl] = out[0];
         S[3 * sl + 1] = out[1];
         S[3 * sl + 2] = out[2];
-        norm[2 * sl] = out[0] > 0.0 ? 1.0 / (s2 * out[0]) : 0.0;
-        norm[2 * sl + 1] = out[1] > 0.0 ? 1.0 / (s2 * out[1]) : 0.0;
+        // F = na |F_a|^2 + nb |F_b|^2 + nab Re(F_a conj F_b)
+        double na = 0.0, nb = 0.0, nab = 0.0;
+        if (full) {
+            const double D = out[0] * out[1] - out[2] * out[2];
+            if (D > 0.0) {
+                na = out[1] / (s2 * D);
+                nb = out[0] / (s2 * D);
+                nab = -2.0 * out[2] / (s2 * D);
+            }
+        } else {
+            na = out[0] > 0.0 ? 1.0 / (s2 * out[0]) : 0.0;
+            nb = out[1] > 0.0 ? 1.0 / (s2 * out[1]) : 0.0;
+        }
+        norm[4 * sl] = na;
+        norm[4 * sl + 1] = nb;
+        norm[4 * sl + 2] = nab;
+        norm[4 * sl + 3] = 0.0;
     }
 }
 
@@ -472,7 +487,7 @@ int launch_geometry(const Plan &p, const BandDev &b, int64_t s0, int64_t ns, boo
 
 int launch_reduce_norms(const Plan &p, const BandDev &b, int64_t ns, double *norm, cudaStream_t s) {
     k_reduce_norms<<<(unsigned)ns, 32, 0, s>>>(p.partials, (int)blocks(b.n, 256), b.sigma2, p.S,
-                                               norm);
+                                               norm, p.desc.statistic == FSTAT_F_FULL ? 1 : 0);
     return 1;
 }
 

@@ -286,7 +286,7 @@ struct GenericStore {
 // GPU.
 template <typename T, class C>
 struct SearchEpi {
-    const double *norm;      // [sky_local][2]
+    const double *norm;      // [sky_local][4]: na, nb, nab (F = na|F_a|^2 + nb|F_b|^2 + nab Re F_a F_b*)
     int n_spin;
     int64_t c0, s0;
     uint32_t cell_base;      // first global cell index of this band
@@ -295,14 +295,15 @@ struct SearchEpi {
     CandRecord *out;
     unsigned long long *count;
     unsigned long long cap;
-    T na, nb;
+    T na, nb, nab;
     uint32_t cell;
     int l2_0;
     __device__ void init() {
         const int64_t c = c0 + blockIdx.y;
         const int64_t sky = c / n_spin;
-        na = (T)norm[2 * (sky - s0)];
-        nb = (T)norm[2 * (sky - s0) + 1];
+        na = (T)norm[4 * (sky - s0)];
+        nb = (T)norm[4 * (sky - s0) + 1];
+        nab = (T)norm[4 * (sky - s0) + 2];
         cell = cell_base + (uint32_t)c;
         l2_0 = blockIdx.x * C::F;
     }
@@ -315,6 +316,7 @@ struct SearchEpi {
 #pragma unroll
         for (int r = 0; r < R; ++r) {
             Fv[r] = (ra[r] * ra[r] + ia[r] * ia[r]) * na + (rb[r] * rb[r] + ib[r] * ib[r]) * nb;
+            if (nab != T(0)) Fv[r] += (ra[r] * rb[r] + ia[r] * ib[r]) * nab;   // full form
             const int64_t bin = (int64_t)C::N2 * (j + r * JPF) + l2;
             const bool p = (bin >= bin_lo) && (bin <= bin_hi) && (T(2) * Fv[r] > thr);
             any |= p;

@@ -235,7 +235,7 @@ struct ScratchLoadTMA {
 // l1 < N1/2 (r < R/2) are used and the rest of the last DFT is never computed.
 template <class C, bool LOWER>
 struct SearchEpi2 {
-    const double *norm;      // [sky_local][2]
+    const double *norm;      // [sky_local][4]: na, nb, nab (F = na|F_a|^2 + nb|F_b|^2 + nab Re F_a F_b*)
     int n_spin;
     int64_t c0, s0;
     uint32_t cell_base;      // first global cell index of this band
@@ -244,14 +244,15 @@ struct SearchEpi2 {
     CandRecord *out;
     unsigned long long *count;
     unsigned long long cap;
-    float na, nb, thr_half;
+    float na, nb, nab, thr_half;
     uint32_t cell;
     int l2_0;
     __device__ void init(int tile, int64_t cl, int64_t) {
         const int64_t c = c0 + cl;
         const int64_t sky = c / n_spin;
-        na = (float)norm[2 * (sky - s0)];
-        nb = (float)norm[2 * (sky - s0) + 1];
+        na = (float)norm[4 * (sky - s0)];
+        nb = (float)norm[4 * (sky - s0) + 1];
+        nab = (float)norm[4 * (sky - s0) + 2];
         cell = cell_base + (uint32_t)c;
         l2_0 = tile * C::F;
         thr_half = 0.5f * thr;   // 2F > thr  <=>  F > thr / 2, both sides exact
@@ -267,13 +268,23 @@ struct SearchEpi2 {
         const int bin0 = C::N2 * (q.j + q.t * H * JPF) + l2_0 + q.f;
         const int lo = (int)bin_lo;
         const unsigned span = (unsigned)(bin_hi - bin_lo);
+        const bool full = nab != 0.f;   // the same for the whole grid
 #pragma unroll
         for (int r = 0; r < H; ++r) {
-            // this lane's |x|^2 at outputs r (a lane's bins) and r + H (b lane's)
-            const float p_lo = re[r] * re[r] + im[r] * im[r];
-            const float p_hi = re[r + H] * re[r + H] + im[r + H] * im[r + H];
-            const float other = __shfl_xor_sync(0xffffffffu, q.t == 0 ? p_hi : p_lo, 16);
-            Fv[r] = q.t == 0 ? p_lo * na + other * nb : other * na + p_hi * nb;
+            if (full) {   // the partner's complex value: the cross term needs it
+                const float sr = q.t == 0 ? re[r + H] : re[r], si = q.t == 0 ? im[r + H] : im[r];
+                const float orr = __shfl_xor_sync(0xffffffffu, sr, 16);
+                const float oi = __shfl_xor_sync(0xffffffffu, si, 16);
+                const float ar = q.t == 0 ? re[r] : orr, ai = q.t == 0 ? im[r] : oi;
+                const float br = q.t == 0 ? orr : re[r + H], bi = q.t == 0 ? oi : im[r + H];
+                Fv[r] = (ar * ar + ai * ai) * na + (br * br + bi * bi) * nb + (ar * br + ai * bi) * nab;
+            } else {
+                // this lane's |x|^2 at outputs r (a lane's bins) and r + H (b lane's)
+                const float p_lo = re[r] * re[r] + im[r] * im[r];
+                const float p_hi = re[r + H] * re[r + H] + im[r + H] * im[r + H];
+                const float other = __shfl_xor_sync(0xffffffffu, q.t == 0 ? p_hi : p_lo, 16);
+                Fv[r] = q.t == 0 ? p_lo * na + other * nb : other * na + p_hi * nb;
+            }
             const unsigned off = (unsigned)(bin0 + r * C::N2 * JPF - lo);
             pr[r] = (off <= span) && (Fv[r] > thr_half);
             any |= pr[r];

@@ -27,6 +27,7 @@ P = C.POINTER
 FSTAT_OK, FSTAT_ERR_ARG, FSTAT_ERR_OOM, FSTAT_ERR_CUDA = 0, 1, 2, 3
 FSTAT_ERR_OVERFLOW, FSTAT_ERR_TIMEOUT, FSTAT_ERR_STATE, FSTAT_ERR_INTERNAL = 4, 5, 6, 7
 FP64_PLAIN, FP32_BATCHED = 0, 1
+F_SIMPLE, F_FULL = 0, 1
 
 
 class fstat_band(C.Structure):
@@ -38,7 +39,8 @@ class fstat_plan_desc(C.Structure):
     _fields_ = [("n_bands", i32), ("bands", P(fstat_band)), ("n_sky", i64), ("alpha", P(f64)),
                 ("delta", P(f64)), ("n_spin", i64), ("fdot", P(f64)), ("thr_2F", f64),
                 ("bin_lo", i64), ("bin_hi", i64), ("lat", f64), ("gamma", f64),
-                ("upsample", i32), ("sigma2", f64), ("form", i32), ("cand_capacity", i64),
+                ("upsample", i32), ("statistic", i32), ("sigma2", f64), ("form", i32),
+                ("cand_capacity", i64),
                 ("cuda_stream", C.c_void_p), ("inputs_on_device", i32)]
 
 
@@ -131,7 +133,7 @@ class Plan:
     def __init__(self, bands: Sequence, alpha, delta, fdot, thr_2F: float, *, lat: float,
                  gamma: float, upsample: int = 2, sigma2: float = 0.0, form: int = FP32_BATCHED,
                  bin_lo: int = 0, bin_hi: int = 0, cand_capacity: int = 1 << 20,
-                 stream: Optional[int] = None, on_device: bool = False):
+                 stream: Optional[int] = None, on_device: bool = False, full: bool = False):
         self._keep = []
         nb = len(bands)
         arr = (fstat_band * nb)()
@@ -176,6 +178,7 @@ class Plan:
         d.thr_2F, d.bin_lo, d.bin_hi = float(thr_2F), int(bin_lo), int(bin_hi)
         d.lat, d.gamma, d.upsample, d.sigma2 = float(lat), float(gamma), int(upsample), float(sigma2)
         d.form, d.cand_capacity = int(form), int(cand_capacity)
+        d.statistic = F_FULL if full else F_SIMPLE
         d.cuda_stream = C.c_void_p(stream) if stream else None
         d.inputs_on_device = 1 if on_device else 0
         self._desc = d

@@ -45,9 +45,9 @@ def _gpu_F(fs, w, form, cells_per_band=None, bins=None, **kw):
     return c, info
 
 
-def _oracle_F(w, band_idx, cells, bin_lo=0, bin_hi=0, sigma2=0.0, upsample=None):
+def _oracle_F(w, band_idx, cells, bin_lo=0, bin_hi=0, sigma2=0.0, upsample=None, full=False):
     b = w.bands[band_idx]
-    prm = O.params(w.lat, w.gamma, upsample or w.upsample, sigma2, False, 0)
+    prm = O.params(w.lat, w.gamma, upsample or w.upsample, sigma2, full, 0)
     cs = np.array([c[0] for c in cells])
     cp = np.array([c[1] for c in cells])
     return O.cells_F(b, prm, w.alpha, w.delta, w.fdot, cs, cp, bin_lo, bin_hi, NTHREADS)
@@ -324,3 +324,47 @@ def test_precision_workload_full_grid_sampled(fs):
         sel = c[(c["sky"] == inj.sky) & (c["spin"] == inj.spin)]
         if inj.snr >= 12:
             assert sel.size and abs(int(sel["bin"][np.argmax(sel["F"])]) - inj.bin) <= 1
+
+
+# ------------------------------------------------------------------ full JKS statistic
+@pytest.mark.parametrize("form", [0, 1])
+def test_full_statistic_all_bins(fs, form):
+    """The full form (with S_ab) on every bin of a small grid, a 4096-sample band
+    with a band offset, against the oracle's full form."""
+    w0 = S.workload(1, n_sky=5, n_spin=2)
+    b = S.make_band(4096, 2.0, 31, 1.0, w0.alpha, w0.delta, w0.fdot, [], f_off=100 + (1 - 2 ** -5) * 3)
+    w = S.Workload("full", [b], w0.alpha, w0.delta, w0.fdot, 10.0)
+    c, _ = _gpu_F(fs, w, form, full=True)
+    cells = [(s, j) for s in range(5) for j in range(2)]
+    ref = _check_all_bins(c, w, form, 0, cells, 1, b.n_fft // 2 - 1, full=True)
+    simple = _oracle_F(w, 0, cells[:1])
+    assert np.max(np.abs(simple[0] - ref[0]) / np.maximum(ref[0], 2.0)) > 1e-3   # the forms differ
+
+
+def test_full_statistic_candidates_two_sidereal_days(fs):
+    """FP32 batched full form, N_fft = 2^18, 2F > 30: candidates of sampled cells
+    (injected and random) against the oracle's full form."""
+    w = S.workload(3, n_sky=64, n_spin=8)
+    p = _plan(fs, w, 1, w.thr_2F, cand_capacity=1 << 24, full=True)
+    assert p.search() == fs.FSTAT_OK
+    c, total = p.candidates()
+    p.close()
+    assert total == c.size
+    rng = np.random.default_rng(9)
+    cells = sorted({(i.sky, i.spin) for i in w.bands[0].injections if i.sky < 64 and i.spin < 8} |
+                   {(int(rng.integers(64)), int(rng.integers(8))) for _ in range(3)})
+    ref = _oracle_F(w, 0, cells, full=True)
+    _compare_candidates_cells(c, w, cells, ref, 1e-4)
+
+
+def _compare_candidates_cells(c, w, cells, ref, tol):
+    for i, (sk, sp) in enumerate(cells):
+        sel = c[(c["sky"] == sk) & (c["spin"] == sp)]
+        want = np.nonzero(2 * ref[i] > w.thr_2F)[0] + 1
+        got = sel["bin"]
+        inband = np.abs(2 * ref[i] - w.thr_2F) <= 2 * tol * np.maximum(ref[i], 2.0)
+        sym = set(want.tolist()) ^ set(got.tolist())
+        assert all(inband[bn - 1] for bn in sym), (sk, sp, sorted(sym)[:10])
+        common = np.intersect1d(want, got)
+        if common.size:
+            assert np.max(_rel_err(sel["F"][np.isin(got, common)], ref[i][common - 1])) <= tol
