@@ -33,7 +33,7 @@ class OrcBand(C.Structure):
 
 class OrcParams(C.Structure):
     _fields_ = [("lat", f64), ("gamma", f64), ("upsample", i32), ("sigma2", f64),
-                ("full_form", i32), ("amp_mode", i32)]
+                ("full_form", i32), ("amp_mode", i32), ("interbin", i32)]
 
 
 class OrcCandidate(C.Structure):
@@ -157,9 +157,9 @@ class _BandRef:
                          _dp(self.r), float(band.phi0), float(getattr(band, "eps", 0.0)), nfft)
 
 
-def params(lat, gamma, upsample=2, sigma2=0.0, full_form=False, amp_mode=0):
+def params(lat, gamma, upsample=2, sigma2=0.0, full_form=False, amp_mode=0, interbin=False):
     return OrcParams(float(lat), float(gamma), int(upsample), float(sigma2), int(full_form),
-                     int(amp_mode))
+                     int(amp_mode), int(interbin))
 
 
 def sky_prepare(band, prm, xu, alpha, delta):

@@ -319,6 +319,28 @@ int orc_cell_F(const orc_band *band, const orc_params *p, const double *y, const
         za[2 * k] = a[k] * wr; za[2 * k + 1] = a[k] * wi;
         zb[2 * k] = b[k] * wr; zb[2 * k + 1] = b[k] * wi;
     }
+    if (p->interbin) {
+        /* interbinning: a transform of half the length (still >= n), even output
+           bins taken as they are, odd bins from the difference of the two
+           neighbours scaled by pi/4 (the value a tone half-way between two
+           Fourier frequencies has there) */
+        const int64_t m = nf / 2;
+        int rc = orc_fft_pow2(za, m, -1);
+        if (!rc) rc = orc_fft_pow2(zb, m, -1);
+        if (!rc)
+            for (int64_t l = bin_lo; l <= bin_hi; ++l) {
+                const int64_t k = l / 2, k1 = (k + 1) % m;
+                double ar = za[2 * k], ai = za[2 * k + 1], br = zb[2 * k], bi = zb[2 * k + 1];
+                if (l % 2) {
+                    const double q = 0.25 * PI_D;
+                    ar = q * (ar - za[2 * k1]); ai = q * (ai - za[2 * k1 + 1]);
+                    br = q * (br - zb[2 * k1]); bi = q * (bi - zb[2 * k1 + 1]);
+                }
+                F[l - bin_lo] = fstat_combine(p, S, sigma2, ar, ai, br, bi);
+            }
+        if (!work) free(za);
+        return rc;
+    }
     int rc = orc_fft_pow2(za, nf, -1);
     if (!rc) rc = orc_fft_pow2(zb, nf, -1);
     if (!rc)

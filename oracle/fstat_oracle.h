@@ -53,6 +53,11 @@ typedef struct {
     double sigma2;      /* noise variance; <= 0: estimate from x */
     int full_form;      /* 0: F with S_aa, S_bb only; 1: full form with S_ab */
     int amp_mode;       /* 0: JKS a(t), b(t); 1: diagnostic a = 1, b = 0 */
+    int interbin;       /* 0: exact zero-padded transform of length n_fft;
+                           1: the paper's "Fourier transform interpolation" (Sect. 2)
+                           read as interbinning: a transform of length M = n_fft/2,
+                           even bins 2k = X(k), odd bins 2k+1 = (pi/4)(X(k) - X(k+1)),
+                           X(M) = X(0) */
 } orc_params;
 
 typedef struct {

@@ -388,3 +388,51 @@ def test_paper_sizes_golden():
     assert 100 + (1 - 2 ** -5) * 100 == rows["f_off_band_100"]
     assert rows["band_overlap_hz"] == 2 ** -5
     assert S.N_2SID == int(2 * S.SIDEREAL_DAY_S / S.DT)
+
+
+# ----------------------------------------------------------------- interbinning
+# The paper's "Fourier transform interpolation ... twice as long" (Sect. 2) as
+# interbinning: a transform of length n_fft / 2, odd bins (pi/4)(X_k - X_{k+1}).
+def test_interbin_even_bins_are_the_zero_padded_ones():
+    """Even bins of the interbinned statistic are the zero-padded transform's
+    (X_{2M}(2k) = X_M(k) for a series of at most M samples): both forms, noise."""
+    b, w = _band()
+    for full in (False, True):
+        F = [O.cells_F(b, O.params(w.lat, w.gamma, 2, 0.0, full, 0, ib), w.alpha, w.delta, w.fdot,
+                       [3, 7], [1, 2], 0, b.n_fft - 1) for ib in (False, True)]
+        assert _rel(F[1][:, 0::2], F[0][:, 0::2]) < 1e-11
+        assert _rel(F[1][:, 1::2], F[0][:, 1::2]) > 1e-3        # odd bins are interpolated
+
+
+def test_interbin_recovers_a_half_bin_tone():
+    """A tone half-way between two Fourier frequencies of the M-point transform
+    (r = 0, a = 1, b = 0, no spindown): the interbinned value at the odd bin
+    equals the zero-padded one to O(1/M^2); the odd bin below it does not."""
+    w = S.workload(1)
+    M, k0 = 4096, 1000
+    b = S.make_band(M, 2.0, 1, 1.0, w.alpha, w.delta, w.fdot, [], n_fft=2 * M)
+    b.r = np.zeros_like(b.r)
+    b.x = np.cos(2 * np.pi * (k0 + 0.5) * np.arange(M) / M)
+    F = [O.cells_F(b, O.params(w.lat, w.gamma, 2, 1.0, False, 1, ib), w.alpha, w.delta,
+                   np.array([0.0]), [0], [0], 0, 2 * M - 1)[0] for ib in (False, True)]
+    assert F[0][2 * k0 + 1] == pytest.approx(M / 4, rel=1e-9)      # |M/2|^2 / (sigma^2 M)
+    assert F[1][2 * k0 + 1] == pytest.approx(F[0][2 * k0 + 1], rel=1e-5)
+    assert F[1][2 * k0 - 1] < 0.2 * F[1][2 * k0 + 1]
+
+
+def test_interbin_noise_level():
+    """White noise, n = M (independent Fourier bins), r = 0, a = 1, b = 0: E[2F] is
+    2 at even bins (the periodogram) and 2 (pi/4)^2 * 2 = pi^2/4 at odd bins."""
+    w = S.workload(1)
+    M = 4096
+    ev, od = [], []
+    for s in range(40):
+        b = S.make_band(M, 2.0, 7000 + s, 1.0, w.alpha, w.delta, w.fdot, [], n_fft=2 * M)
+        b.r = np.zeros_like(b.r)
+        F = O.cells_F(b, O.params(w.lat, w.gamma, 1, 1.0, False, 1, True), w.alpha, w.delta,
+                      np.array([0.0]), [0], [0], 0, 2 * M - 1, 1)[0]
+        ev.append(2 * F[2:M:2])
+        od.append(2 * F[1:M:2])
+    ev, od = np.concatenate(ev), np.concatenate(od)
+    assert abs(ev.mean() - 2.0) < 4 * ev.std() / math.sqrt(ev.size)
+    assert abs(od.mean() - math.pi ** 2 / 4) < 4 * od.std() / math.sqrt(od.size)
