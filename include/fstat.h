@@ -89,6 +89,16 @@ typedef struct {
    S_aa, S_bb, S_ab are the sums of a^2, b^2, a b over the resampled window. */
 typedef enum { FSTAT_F_SIMPLE = 0, FSTAT_F_FULL = 1 } fstat_statistic;
 
+/* How the transform "twice as long" of Sect. 2 is formed.  FSTAT_INTERP_ZEROPAD:
+   exact zero-padded transforms of length n_fft.  FSTAT_INTERP_INTERBIN: the
+   paper's interpolation read as interbinning -- transforms of length n_fft / 2
+   (still >= n), output bin 2k = X(k), bin 2k+1 = (pi/4)(X(k) - X(k+1)), X(n_fft/2)
+   = X(0); the bins keep the n_fft grid.  About half the transform work; the odd
+   bins are an approximation (exact for a tone half-way between Fourier
+   frequencies, and a noise level of pi^2/4 per transform instead of 2).
+   FSTAT_FP32_BATCHED only, n_fft in 2^13 .. 2^20. */
+typedef enum { FSTAT_INTERP_ZEROPAD = 0, FSTAT_INTERP_INTERBIN = 1 } fstat_interpolation;
+
 typedef struct {
     int n_bands;                 /* >= 1 */
     const fstat_band *bands;     /* [n_bands] */
@@ -107,6 +117,7 @@ typedef struct {
     int statistic;               /* FSTAT_F_SIMPLE (0) or FSTAT_F_FULL (1), see below */
     double sigma2;               /* noise variance; <= 0: (1/N) sum x^2 per band */
     fstat_form form;
+    int interpolation;           /* FSTAT_INTERP_ZEROPAD (0) or FSTAT_INTERP_INTERBIN (1) */
     int64_t cand_capacity;       /* device candidate records kept per search, >= 1 */
     void *cuda_stream;           /* cudaStream_t to run on, or NULL (the plan's own) */
     int inputs_on_device;        /* 0: x/x32/r/alpha/delta/fdot are host pointers;

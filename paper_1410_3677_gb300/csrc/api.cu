@@ -114,6 +114,12 @@ fstat_status validate(const fstat_plan_desc *d, std::string &err) {
     if (d->n_spin < 1 || !d->fdot) { err = "need n_spin >= 1 and fdot"; return FSTAT_ERR_ARG; }
     if (d->form != FSTAT_FP64_PLAIN && d->form != FSTAT_FP32_BATCHED) { err = "unknown form"; return FSTAT_ERR_ARG; }
     if (d->statistic != FSTAT_F_SIMPLE && d->statistic != FSTAT_F_FULL) { err = "unknown statistic"; return FSTAT_ERR_ARG; }
+    if (d->interpolation != FSTAT_INTERP_ZEROPAD && d->interpolation != FSTAT_INTERP_INTERBIN) {
+        err = "unknown interpolation"; return FSTAT_ERR_ARG;
+    }
+    if (d->interpolation == FSTAT_INTERP_INTERBIN && d->form != FSTAT_FP32_BATCHED) {
+        err = "interbinning needs the FP32 batched form"; return FSTAT_ERR_ARG;
+    }
     if (d->upsample < 1 || d->upsample > 8) { err = "upsample must be 1..8"; return FSTAT_ERR_ARG; }
     if (d->cand_capacity < 1 || d->cand_capacity > (int64_t(1) << 34)) { err = "cand_capacity out of range"; return FSTAT_ERR_ARG; }
     if (!is_finite(d->thr_2F) || !is_finite(d->lat) || !is_finite(d->gamma) || !is_finite(d->sigma2)) {
@@ -134,6 +140,9 @@ fstat_status validate(const fstat_plan_desc *d, std::string &err) {
         if (nf == 0) { nf = 1; while (nf < 2 * b.n) nf <<= 1; }
         const int lg = ilog2_exact(nf);
         if (lg < kMinLogN || lg > kMaxLogN || nf < 2 * b.n) { err = band_err(i, "n_fft must be a power of two >= 2n in [256, 2^20]"); return FSTAT_ERR_ARG; }
+        if (d->interpolation == FSTAT_INTERP_INTERBIN && !interbin_supported(lg)) {
+            err = band_err(i, "interbinning needs n_fft in [2^13, 2^20]"); return FSTAT_ERR_ARG;
+        }
         if (d->bin_lo != 0 || d->bin_hi != 0) {
             if (d->bin_lo < 0 || d->bin_hi < d->bin_lo || d->bin_hi >= nf) { err = band_err(i, "bin range outside [0, n_fft)"); return FSTAT_ERR_ARG; }
         }
@@ -200,6 +209,7 @@ void create_impl(Plan &p, const fstat_plan_desc *d) {
     p.desc = *d;
     const bool dev = d->inputs_on_device == 1;
     const bool fp32 = d->form == FSTAT_FP32_BATCHED;
+    p.interbin = d->interpolation == FSTAT_INTERP_INTERBIN;
     if (d->cuda_stream) {
         p.stream = (cudaStream_t)d->cuda_stream;
     } else {
@@ -232,6 +242,7 @@ void create_impl(Plan &p, const fstat_plan_desc *d) {
         if (b.n_fft == 0) { b.n_fft = 1; while (b.n_fft < 2 * b.n) b.n_fft <<= 1; }
         b.logn = ilog2_exact(b.n_fft);
         need(b.logn);
+        if (d->interpolation == FSTAT_INTERP_INTERBIN) need(b.logn - 1);
         if (d->bin_lo == 0 && d->bin_hi == 0) { b.lo = 1; b.hi = b.n_fft / 2 - 1; }
         else { b.lo = d->bin_lo; b.hi = d->bin_hi; }
         // upsample transforms: a power of two >= 256 directly, else Bluestein
@@ -522,8 +533,10 @@ void enqueue_search(Plan &p, int64_t begin, int64_t end) {
         join_workers();   // the prologue's transforms use the scratch area
         band_prologue(p, b);
         const int64_t s_first = lc0 / d.n_spin, s_last = (lc1 - 1) / d.n_spin;
-        const double nfft = (double)b.n_fft;
-        const double lg1 = (double)log_n1(b.logn), lg2 = (double)log_n2(b.logn);
+        // transform length of the search (half of n_fft when interbinning)
+        const int tlog = p.interbin ? b.logn - 1 : b.logn;
+        const double nfft = (double)(int64_t(1) << tlog);
+        const double lg1 = (double)log_n1(tlog), lg2 = (double)log_n2(tlog);
         const int i_geo = stat_index(p, "geometry_resample");
         const int i_p1 = stat_index(p, fp32 ? "fft_pass1_f32" : "fft_pass1_f64");
         const int i_p2 = stat_index(p, fp32 ? "fft_pass2_fstat_f32" : "fft_pass2_fstat_f64");
@@ -547,7 +560,7 @@ void enqueue_search(Plan &p, int64_t begin, int64_t end) {
             if (tg) { rec_timing(g1, s); p.pending.push_back({i_geo, g0, g1}); }
             const int64_t c_lo = std::max<int64_t>(lc0, sb * d.n_spin);
             const int64_t c_hi = std::min<int64_t>(lc1, (sb + ns) * d.n_spin);
-            if (fp32 && p.use_persistent && persistent_supported(b.logn)) {
+            if (fp32 && p.use_persistent && !p.interbin && persistent_supported(b.logn)) {
                 join_workers();
                 const bool tp = stat_launch(p, i_pp, 2.0 * (c_hi - c_lo) * 5.0 * nfft * (lg1 + lg2),
                                             (double)ns * b.n * welem);

@@ -114,6 +114,7 @@ struct Plan {
     int elems_per_thread = 16;     // FP32 batched passes: 16 or 8 complex elements per thread
     int engine = 2;                // FP32 batched passes, 2^12 .. 2^19: 2 = two-stage engine, 1 = radix-8 engine
     bool fused = false;            // two-stage engine: both passes in one ticket-ordered launch
+    bool interbin = false;         // FSTAT_INTERP_INTERBIN: half-length transforms + interbinning
     uint32_t *fctl = nullptr;      // per worker: 1 + 2 * cell_batch counters of the fused launch
     size_t slot_cells = 0;         // cells of scratch per worker (>= cell_batch, >= the fused ring)
     int fused_slots = kFusedSlots, fused_ahead = kFusedAhead;
@@ -234,6 +235,9 @@ inline cudaError_t record_timing_event(cudaEvent_t e, cudaStream_t s) {
     return cudaEventRecordWithFlags(e, s, cs == cudaStreamCaptureStatusActive ? cudaEventRecordExternal
                                                                                : cudaEventRecordDefault);
 }
+// Whether a band of transform length 2^logn (the n_fft bin grid) can run in the
+// interbinning form (a half-length transform of 2^12 .. 2^19).
+bool interbin_supported(int logn);
 // Whether the FP32 cells of a band of length 2^logn run as one fused launch.
 bool fused_supported(const Plan &p, int logn);
 // `mid` (may be null) is recorded between the two passes.

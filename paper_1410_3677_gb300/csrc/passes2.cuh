@@ -311,14 +311,133 @@ struct SearchEpi2 {
 // keeps no demodulation or twiddle-power state) and 3 x 68 KB of shared memory.
 // Pass 1 of a search transform (N_fft >= 2n) reads only the first half of each
 // column: elements k2 >= N2/2 lie at k >= N/2 >= n, in the zero padding.
-template <int LOGN, int PASS, int MAPM, class LD, class ST, int TS = 256>
+// ZH1 = false: pass 1 of a transform only as long as the series allows (the
+// half-length transform of the interbinning form, N >= n but not N >= 2n).
+template <int LOGN, int PASS, int MAPM, class LD, class ST, int TS = 256, bool ZH1 = true>
 __global__ void __launch_bounds__(TS, 768 / TS) k_pass2(LD ld, ST st, const float *__restrict__ tw) {
     using C = Cfg2<LOGN, PASS, TS>;
     if constexpr (PASS == 2) ld.prefetch_ahead();
     ld.init(blockIdx.x, blockIdx.y, blockIdx.y);
     st.init(blockIdx.x, blockIdx.y, blockIdx.y);
     if constexpr (eng2::LoaderStaged<LD>::value) ld.stage();
-    eng2::run_pass<float, C::M, C::SEQ, C::EH, -1, MAPM, LD, ST, PASS == 1>(ld, st, tw);
+    eng2::run_pass<float, C::M, C::SEQ, C::EH, -1, MAPM, LD, ST, PASS == 1 && ZH1>(ld, st, tw);
+}
+
+// ------------------------------------------------------------------ interbinning
+// The paper's Fourier-transform interpolation to a transform twice as long
+// (Sect. 2) as interbinning: the search transform has length N = n_fft / 2 and
+// output bin 2k of the n_fft grid is X(k), bin 2k + 1 is (pi/4)(X(k) - X(k + 1)),
+// X(N) = X(0).  With k = N2 l1 + l2, X(k + 1) sits in row l2 + 1 (or, for the
+// last row, in row 0 at l1 + 1), so a pass-2 tile of F rows starts F - 1 rows
+// after the previous one: its last row only serves as the neighbour of the row
+// before it.  Rows past N2 are rows of the next l1 (wrapped).
+
+// Pass 2 input of the interbinning form: row (l2_0 + f) mod N2 of transform t.
+template <class C>
+struct ScratchLoadIB {
+    const float2 *scratch;
+    const float2 *base;
+    int l2_0;
+    __device__ void init(int tile, int64_t, int64_t slot) {
+        base = scratch + slot * 2 * C::N;
+        l2_0 = tile * (C::F - 1);
+    }
+    template <int R, int JPF>
+    __device__ __forceinline__ void load(const eng2::Job &q, float *re, float *im) const {
+        const int l2 = (l2_0 + q.f) & (C::N2 - 1);
+        const float2 *row = base + (int64_t)q.t * C::N + (int64_t)l2 * C::N1 + q.j;
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const float2 v = __ldcg(row + r * JPF);
+            re[r] = v.x; im[r] = v.y;
+        }
+    }
+};
+
+// Keeps each row's outputs X(l1) in the warp's own exchange row (free once the
+// warp has gathered its stage-1 inputs; rows of the warp mapping belong to one
+// warp), element l1 at pad(l1).
+template <class C>
+struct StoreRowsSmem {
+    __device__ void init(int, int64_t, int64_t) {}
+    template <int R, int JPF>
+    __device__ __forceinline__ void store(const eng2::Job &q, float *re, float *im) const {
+        __syncwarp();
+        float2 *row = reinterpret_cast<float2 *>(eng2::dyn_smem()) + q.s * eng2::row_ld(C::M);
+#pragma unroll
+        for (int r = 0; r < R; ++r) row[eng2::pad(q.j + r * JPF)] = float2{re[r], im[r]};
+    }
+};
+
+template <int LOGN, int TS = 256>
+struct IBGeom {
+    using C = Cfg2<LOGN, 2, TS>;
+    static constexpr int STEP = C::F - 1;                    // rows emitted per tile
+    static constexpr int TILES = (C::N2 + STEP - 1) / STEP;
+};
+
+template <int LOGN, int TS = 256>
+__global__ void __launch_bounds__(TS, 768 / TS)
+k_pass2_ib(ScratchLoadIB<Cfg2<LOGN, 2, TS>> ld, SearchEpi2<Cfg2<LOGN, 2, TS>, false> ep,
+           const float *__restrict__ tw) {
+    using C = Cfg2<LOGN, 2, TS>;
+    ld.init(blockIdx.x, blockIdx.y, blockIdx.y);
+    ep.init(0, blockIdx.y, blockIdx.y);
+    StoreRowsSmem<C> st;
+    eng2::run_pass<float, C::M, C::SEQ, C::EH, -1, eng2::kMapW, ScratchLoadIB<C>, StoreRowsSmem<C>, false>(
+        ld, st, tw);
+    __syncthreads();
+    const float2 *X = reinterpret_cast<const float2 *>(eng2::dyn_smem());
+    constexpr int RL = eng2::row_ld(C::M);
+    constexpr int F = C::F, N1 = C::N1, N2 = C::N2;
+    constexpr int PAIRS = (F - 1) * N1;
+    constexpr float Q = 0.78539816339744831f;   // pi / 4
+    const int l2_0 = blockIdx.x * (F - 1);
+    const int lane = threadIdx.x & 31;
+    const bool full = ep.nab != 0.f;
+    const int lo = (int)ep.bin_lo;
+    const unsigned span = (unsigned)(ep.bin_hi - ep.bin_lo);
+#pragma unroll 1
+    for (int p0 = 0; p0 < PAIRS; p0 += C::THREADS) {
+        const int pr = p0 + (int)threadIdx.x;
+        const int f = pr / N1, l1 = pr - f * N1;
+        const int l2 = l2_0 + f;
+        const bool own = pr < PAIRS && l2 < N2;
+        float Fe = 0.f, Fo = 0.f;
+        int k = 0;
+        if (own) {
+            // neighbour X(k + 1): row f + 1 at l1, or row 0 of l1 + 1 past the last row
+            const int l1n = (l2 + 1 == N2) ? ((l1 + 1) & (N1 - 1)) : l1;
+            const float2 a0 = X[f * RL + eng2::pad(l1)], b0 = X[(F + f) * RL + eng2::pad(l1)];
+            const float2 a1 = X[(f + 1) * RL + eng2::pad(l1n)], b1 = X[(F + f + 1) * RL + eng2::pad(l1n)];
+            const float ar = Q * (a0.x - a1.x), ai = Q * (a0.y - a1.y);
+            const float br = Q * (b0.x - b1.x), bi = Q * (b0.y - b1.y);
+            Fe = (a0.x * a0.x + a0.y * a0.y) * ep.na + (b0.x * b0.x + b0.y * b0.y) * ep.nb;
+            Fo = (ar * ar + ai * ai) * ep.na + (br * br + bi * bi) * ep.nb;
+            if (full) {
+                Fe += (a0.x * b0.x + a0.y * b0.y) * ep.nab;
+                Fo += (ar * br + ai * bi) * ep.nab;
+            }
+            k = N2 * l1 + l2;
+        }
+#pragma unroll
+        for (int o = 0; o < 2; ++o) {
+            const int bin = 2 * k + o;
+            const float Fv = o ? Fo : Fe;
+            const bool hit = own && (unsigned)(bin - lo) <= span && Fv > ep.thr_half;
+            const unsigned m = __ballot_sync(0xffffffffu, hit);
+            if (m) {
+                const int leader = __ffs(m) - 1;
+                unsigned long long b0v = 0;
+                if (lane == leader) b0v = atomicAdd(ep.count, (unsigned long long)__popc(m));
+                b0v = __shfl_sync(0xffffffffu, b0v, leader);
+                if (hit) {
+                    const unsigned long long idx = b0v + __popc(m & ((1u << lane) - 1u));
+                    if (idx < ep.cap) ep.out[idx] = CandRecord{ep.cell, (uint32_t)bin, (double)Fv};
+                }
+            }
+        }
+    }
 }
 
 // ------------------------------------------------------------------ fused launch

@@ -132,13 +132,66 @@ int launch_search2(const Plan &p, int band_idx, const BandDev &b, int64_t s0, in
                  : launch_two<LOGN, false>(p, band_idx, b, s0, c0, nc, s, mid, cb, ld1, st1, ld2, tw);
 }
 
+// Interbinning form: both passes at length 2^LOGN = n_fft / 2 (pass 1 without
+// the zero-half assumption), pass 2 in overlapping row tiles.
+template <int LOGN>
+int launch_interbin(const Plan &p, int band_idx, const BandDev &b, int64_t s0, int64_t c0,
+                    int64_t nc, cudaStream_t s, cudaEvent_t mid, const CellBufs &cb) {
+    using C1 = Cfg2<LOGN, 1>;
+    using C2 = Cfg2<LOGN, 2>;
+    const TwiddleSet *tw = p.twiddles(LOGN);
+    const int n_spin = (int)p.desc.n_spin;
+    SearchLoad2<C1> ld1{};
+    ld1.w = reinterpret_cast<const float4 *>(cb.w);
+    ld1.w_stride = p.w_stride;
+    ld1.n = (int)b.n;
+    ld1.chirp = p.chirp_fx + (int64_t)band_idx * n_spin;
+    ld1.n_spin = n_spin;
+    ld1.c0 = c0;
+    ld1.s0 = s0;
+    ScratchStore2<C1> st1{};
+    st1.scratch = reinterpret_cast<float2 *>(cb.scratch);
+    st1.lo = tw->lo_f;
+    st1.hi = tw->hi_f;
+    auto k1 = k_pass2<LOGN, 1, eng2::kMapFJ, SearchLoad2<C1>, ScratchStore2<C1>, 256, false>;
+    static bool attr1 = false;
+    if (!attr1) { set_smem(k1, C1::SMEM); attr1 = true; }
+    k1<<<dim3(C1::TILES, (unsigned)nc), C1::THREADS, C1::SMEM, s>>>(ld1, st1, tw->in2_f);
+    if (mid) record_timing_event(mid, s);
+    ScratchLoadIB<C2> ld2{};
+    ld2.scratch = reinterpret_cast<const float2 *>(cb.scratch);
+    const auto ep = make_epi<LOGN, false>(p, band_idx, b, c0, s0, cb);
+    auto k2 = k_pass2_ib<LOGN>;
+    static bool attr2 = false;
+    if (!attr2) { set_smem(k2, C2::SMEM); attr2 = true; }
+    k2<<<dim3(IBGeom<LOGN>::TILES, (unsigned)nc), C2::THREADS, C2::SMEM, s>>>(ld2, ep, tw->in1_f);
+    return 2;
+}
+
 }  // namespace
 
-bool fused_supported(const Plan &p, int logn) { return p.engine == 2 && p.fused && logn >= 12 && logn <= 19; }
+bool interbin_supported(int logn) { return logn - 1 >= 12 && logn - 1 <= 19; }
+
+bool fused_supported(const Plan &p, int logn) {
+    return p.engine == 2 && p.fused && !p.interbin && logn >= 12 && logn <= 19;
+}
 
 int launch_search_cells_f32(const Plan &p, int band_idx, const BandDev &b, int64_t s0,
                             int64_t c0, int64_t nc, cudaStream_t s, cudaEvent_t mid,
                             const CellBufs &cb) {
+    if (p.interbin) {
+        switch (b.logn - 1) {
+            case 12: return launch_interbin<12>(p, band_idx, b, s0, c0, nc, s, mid, cb);
+            case 13: return launch_interbin<13>(p, band_idx, b, s0, c0, nc, s, mid, cb);
+            case 14: return launch_interbin<14>(p, band_idx, b, s0, c0, nc, s, mid, cb);
+            case 15: return launch_interbin<15>(p, band_idx, b, s0, c0, nc, s, mid, cb);
+            case 16: return launch_interbin<16>(p, band_idx, b, s0, c0, nc, s, mid, cb);
+            case 17: return launch_interbin<17>(p, band_idx, b, s0, c0, nc, s, mid, cb);
+            case 18: return launch_interbin<18>(p, band_idx, b, s0, c0, nc, s, mid, cb);
+            case 19: return launch_interbin<19>(p, band_idx, b, s0, c0, nc, s, mid, cb);
+            default: return -1;
+        }
+    }
     if (p.engine == 2) {
         switch (b.logn) {
             case 12: return launch_search2<12>(p, band_idx, b, s0, c0, nc, s, mid, cb);

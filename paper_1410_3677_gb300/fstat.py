@@ -28,6 +28,7 @@ FSTAT_OK, FSTAT_ERR_ARG, FSTAT_ERR_OOM, FSTAT_ERR_CUDA = 0, 1, 2, 3
 FSTAT_ERR_OVERFLOW, FSTAT_ERR_TIMEOUT, FSTAT_ERR_STATE, FSTAT_ERR_INTERNAL = 4, 5, 6, 7
 FP64_PLAIN, FP32_BATCHED = 0, 1
 F_SIMPLE, F_FULL = 0, 1
+INTERP_ZEROPAD, INTERP_INTERBIN = 0, 1
 
 
 class fstat_band(C.Structure):
@@ -40,7 +41,7 @@ class fstat_plan_desc(C.Structure):
                 ("delta", P(f64)), ("n_spin", i64), ("fdot", P(f64)), ("thr_2F", f64),
                 ("bin_lo", i64), ("bin_hi", i64), ("lat", f64), ("gamma", f64),
                 ("upsample", i32), ("statistic", i32), ("sigma2", f64), ("form", i32),
-                ("cand_capacity", i64),
+                ("interpolation", i32), ("cand_capacity", i64),
                 ("cuda_stream", C.c_void_p), ("inputs_on_device", i32)]
 
 
@@ -133,7 +134,8 @@ class Plan:
     def __init__(self, bands: Sequence, alpha, delta, fdot, thr_2F: float, *, lat: float,
                  gamma: float, upsample: int = 2, sigma2: float = 0.0, form: int = FP32_BATCHED,
                  bin_lo: int = 0, bin_hi: int = 0, cand_capacity: int = 1 << 20,
-                 stream: Optional[int] = None, on_device: bool = False, full: bool = False):
+                 stream: Optional[int] = None, on_device: bool = False, full: bool = False,
+                 interbin: bool = False):
         self._keep = []
         nb = len(bands)
         arr = (fstat_band * nb)()
@@ -179,6 +181,7 @@ class Plan:
         d.lat, d.gamma, d.upsample, d.sigma2 = float(lat), float(gamma), int(upsample), float(sigma2)
         d.form, d.cand_capacity = int(form), int(cand_capacity)
         d.statistic = F_FULL if full else F_SIMPLE
+        d.interpolation = INTERP_INTERBIN if interbin else INTERP_ZEROPAD
         d.cuda_stream = C.c_void_p(stream) if stream else None
         d.inputs_on_device = 1 if on_device else 0
         self._desc = d

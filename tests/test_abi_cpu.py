@@ -102,6 +102,8 @@ def _status(fs, bands, **kw):
     dict(bands=[_B()], bin_lo=5, bin_hi=3),
     dict(bands=[_B()], bin_lo=0, bin_hi=256),                 # >= n_fft (auto 128... 256)
     dict(bands=[_B()], fdot=np.zeros(0)),
+    dict(bands=[_B(n=4096)], interbin=True, form=0),          # interbinning: FP32 form only
+    dict(bands=[_B()], interbin=True, form=1),                # interbinning: n_fft >= 2^13
 ])
 def test_invalid_arguments_rejected_without_gpu(fs, case):
     bands = case.pop("bands")

@@ -45,9 +45,10 @@ def _gpu_F(fs, w, form, cells_per_band=None, bins=None, **kw):
     return c, info
 
 
-def _oracle_F(w, band_idx, cells, bin_lo=0, bin_hi=0, sigma2=0.0, upsample=None, full=False):
+def _oracle_F(w, band_idx, cells, bin_lo=0, bin_hi=0, sigma2=0.0, upsample=None, full=False,
+              interbin=False):
     b = w.bands[band_idx]
-    prm = O.params(w.lat, w.gamma, upsample or w.upsample, sigma2, full, 0)
+    prm = O.params(w.lat, w.gamma, upsample or w.upsample, sigma2, full, 0, interbin)
     cs = np.array([c[0] for c in cells])
     cp = np.array([c[1] for c in cells])
     return O.cells_F(b, prm, w.alpha, w.delta, w.fdot, cs, cp, bin_lo, bin_hi, NTHREADS)
@@ -368,3 +369,40 @@ def _compare_candidates_cells(c, w, cells, ref, tol):
         common = np.intersect1d(want, got)
         if common.size:
             assert np.max(_rel_err(sel["F"][np.isin(got, common)], ref[i][common - 1])) <= tol
+
+
+# ------------------------------------------------------------------ interbinning
+@pytest.mark.parametrize("n,n_fft,full,lohi", [(4096, 1 << 13, False, None), (4096, 1 << 13, True, None),
+                                               (3000, 1 << 13, False, (0, (1 << 13) - 1)),
+                                               (86164, 1 << 18, False, None)])
+def test_interbin_all_bins(fs, n, n_fft, full, lohi):
+    """The interbinning form (half-length transforms, odd bins (pi/4)(X_k - X_k+1))
+    on every bin against the oracle's: default and full bin range (the wrap of
+    the last bin to X(0)), simple and full statistic, short and two-day bands."""
+    w0 = S.workload(1, n_sky=3, n_spin=2)
+    b = S.make_band(n, 2.0, 17 + n, 1.0, w0.alpha, w0.delta, w0.fdot, [], n_fft=n_fft,
+                    f_off=100 + (1 - 2 ** -5) * 5)
+    w = S.Workload("ib", [b], w0.alpha, w0.delta, w0.fdot, 10.0)
+    kw = dict(full=full, interbin=True)
+    if lohi:
+        kw.update(bin_lo=lohi[0], bin_hi=lohi[1])
+    c, _ = _gpu_F(fs, w, 1, **kw)
+    cells = [(s, j) for s in range(3) for j in range(2)]
+    lo, hi = lohi if lohi else (1, n_fft // 2 - 1)
+    _check_all_bins(c, w, 1, 0, cells, lo, hi, full=full, interbin=True)
+
+
+def test_interbin_candidates_two_sidereal_days(fs):
+    """Interbinning form, 2^18 bins, 2F > 30: candidates of sampled cells against
+    the oracle's interbinning form; injections found near their bins."""
+    w = S.workload(3, n_sky=64, n_spin=8)
+    p = _plan(fs, w, 1, w.thr_2F, cand_capacity=1 << 24, interbin=True)
+    assert p.search() == fs.FSTAT_OK
+    c, total = p.candidates()
+    p.close()
+    assert total == c.size
+    rng = np.random.default_rng(11)
+    cells = sorted({(i.sky, i.spin) for i in w.bands[0].injections if i.sky < 64 and i.spin < 8} |
+                   {(int(rng.integers(64)), int(rng.integers(8))) for _ in range(3)})
+    ref = _oracle_F(w, 0, cells, interbin=True)
+    _compare_candidates_cells(c, w, cells, ref, 1e-4)
