@@ -336,6 +336,31 @@ def run_ours(args, rank, world, dist):
                 "sample": f"{sub} sky x {w.n_spin} spindown subgrid of the same workload, "
                           f"one cell per launch pair"}
 
+    # ---------------------------------------------------------------- interbinning form, same grid
+    interbin = None
+    if not args.skip_interbin:
+        pib = fstat.Plan(w.bands, w.alpha, w.delta, w.fdot, w.thr_2F, lat=w.lat, gamma=w.gamma,
+                         upsample=w.upsample, form=fstat.FP32_BATCHED,
+                         cand_capacity=args.cand_capacity, stream=stream.cuda_stream, interbin=True)
+        for _ in range(2):
+            pib.search()                      # the second run captures the graph
+        ib_ms = []
+        for _ in range(max(1, min(args.steps, 3))):
+            with torch.cuda.stream(stream):
+                flush.add_(1.0)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            pib.search()
+            e1.record(stream)
+            e1.synchronize()
+            ib_ms.append(e0.elapsed_time(e1))
+        pib.close()
+        interbin = {"value": nb_total / (statistics.mean(ib_ms) / 1e3), "unit": UNIT,
+                    "ms_per_step": statistics.mean(ib_ms),
+                    "form": "interbinning: transforms of n_fft/2, odd bins (pi/4)(X_k - X_k+1) "
+                            "(the paper's Fourier-transform interpolation; approximate odd bins)"}
+
     # ---------------------------------------------------------------- end to end through the C ABI
     e2e = None
     if not args.skip_e2e:
@@ -396,7 +421,7 @@ def run_ours(args, rank, world, dist):
                        "tuning": tuning,
                        "wall_s": round(t_wall, 3)},
             "candidates": int(n_total), "gpu_launches": int(launches),
-            "roofline": roofline, "fp64_plain": fp64,
+            "roofline": roofline, "fp64_plain": fp64, "interbin": interbin,
             "speedup_vs_fp64_plain": (value / world / fp64["value"]) if fp64 else None,
             "e2e": e2e, "cpu_baseline": cpu, "clocks": clk}
     print(json.dumps(line), flush=True)
@@ -413,6 +438,7 @@ def main():
     ap.add_argument("--skip-fp64", action="store_true")
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--skip-interbin", action="store_true")
     ap.add_argument("--n-sky", type=int, default=0, help="first n sky positions only (profiling)")
     ap.add_argument("--cand-capacity", type=int, default=1 << 27)
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shapes")
