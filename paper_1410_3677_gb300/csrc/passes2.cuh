@@ -354,6 +354,79 @@ struct ScratchLoadIB {
     }
 };
 
+// The same rows staged by the TMA unit: per transform one bulk copy of the rows
+// l2_0 .. N2 - 1 that the tile holds and, for the last tile, one of the rows it
+// wraps to from row 0; the tile F - 1 rows ahead is prefetched into L2.
+template <class C>
+struct ScratchLoadIBTMA {
+    static constexpr bool kStaged = true;
+    const float2 *scratch;
+    int64_t pf_dist;
+    uint32_t *err;
+    const float2 *base;
+    const float2 *rows;
+    uint64_t *bar;
+    int l2_0;
+    __device__ void init(int tile, int64_t, int64_t slot) {
+        base = scratch + slot * 2 * C::N;
+        l2_0 = tile * (C::F - 1);
+        unsigned char *sm = eng2::dyn_smem();
+        rows = reinterpret_cast<const float2 *>(sm);
+        bar = reinterpret_cast<uint64_t *>(sm + C::SMEM);
+    }
+    __device__ void prefetch_ahead() const {
+        if (pf_dist <= 0 || threadIdx.x != 0) return;
+        const int64_t b = blockIdx.x + (int64_t)gridDim.x * blockIdx.y + pf_dist;
+        const int64_t total = (int64_t)gridDim.x * gridDim.y;
+        if (b >= total) return;
+        const int64_t slot = b / gridDim.x;
+        const int l2 = (int)(b - slot * gridDim.x) * (C::F - 1);
+        const int nr = C::N2 - l2 < C::F ? C::N2 - l2 : C::F;
+        const float2 *r = scratch + slot * 2 * C::N + (int64_t)l2 * C::N1;
+        const uint32_t bytes = (uint32_t)(nr * C::N1 * sizeof(float2));
+        ptx::bulk_prefetch_l2(r, bytes);
+        ptx::bulk_prefetch_l2(r + C::N, bytes);
+    }
+    __device__ void stage() const {
+        static_assert(2 * C::F * C::N1 * sizeof(float2) <= eng2::exch_bytes<float, C::M, C::SEQ>(),
+                      "staged rows fit the exchange area");
+        if (threadIdx.x == 0) {
+            ptx::mbar_init(bar, 1);
+            ptx::fence_mbar_init();
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            const int na = C::N2 - l2_0 < C::F ? C::N2 - l2_0 : C::F;   // rows before the wrap
+            const uint32_t row_bytes = (uint32_t)(C::N1 * sizeof(float2));
+            ptx::mbar_arrive_expect_tx(bar, 2 * C::F * row_bytes);
+            for (int t = 0; t < 2; ++t) {
+                float2 *dst = const_cast<float2 *>(rows) + t * C::F * C::N1;
+                const float2 *plane = base + (int64_t)t * C::N;
+                ptx::bulk_g2s(dst, plane + (int64_t)l2_0 * C::N1, na * row_bytes, bar);
+                if (na < C::F) ptx::bulk_g2s(dst + na * C::N1, plane, (C::F - na) * row_bytes, bar);
+            }
+        }
+    }
+    template <int R, int JPF>
+    __device__ __forceinline__ void load(const eng2::Job &q, float *re, float *im) const {
+        if (!ptx::mbar_try_wait(bar, 0)) {
+            const uint64_t t0 = ptx::globaltimer_ns();
+            bool late = false;
+            while (!ptx::mbar_try_wait(bar, 0)) {
+                const uint64_t dt = ptx::globaltimer_ns() - t0;
+                if (!late && dt > 1000000000ull) { atomicExch(err, 1u); late = true; }
+                if (dt > 2000000000ull) break;   // reported above; results are discarded
+            }
+        }
+        const float2 *row = rows + (q.t * C::F + q.f) * C::N1 + q.j;
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const float2 v = row[r * JPF];
+            re[r] = v.x; im[r] = v.y;
+        }
+    }
+};
+
 // Keeps each row's outputs X(l1) in the warp's own exchange row (free once the
 // warp has gathered its stage-1 inputs; rows of the warp mapping belong to one
 // warp), element l1 at pad(l1).
@@ -376,21 +449,24 @@ struct IBGeom {
     static constexpr int TILES = (C::N2 + STEP - 1) / STEP;
 };
 
-template <int LOGN, int TS = 256>
+template <int LOGN, int TS, class LD>
 __global__ void __launch_bounds__(TS, 768 / TS)
-k_pass2_ib(ScratchLoadIB<Cfg2<LOGN, 2, TS>> ld, SearchEpi2<Cfg2<LOGN, 2, TS>, false> ep,
-           const float *__restrict__ tw) {
+k_pass2_ib(LD ld, SearchEpi2<Cfg2<LOGN, 2, TS>, false> ep, const float *__restrict__ tw) {
     using C = Cfg2<LOGN, 2, TS>;
+    if constexpr (eng2::LoaderStaged<LD>::value) ld.prefetch_ahead();
     ld.init(blockIdx.x, blockIdx.y, blockIdx.y);
     ep.init(0, blockIdx.y, blockIdx.y);
+    if constexpr (eng2::LoaderStaged<LD>::value) ld.stage();
     StoreRowsSmem<C> st;
-    eng2::run_pass<float, C::M, C::SEQ, C::EH, -1, eng2::kMapW, ScratchLoadIB<C>, StoreRowsSmem<C>, false>(
-        ld, st, tw);
+    eng2::run_pass<float, C::M, C::SEQ, C::EH, -1, eng2::kMapW, LD, StoreRowsSmem<C>, false>(ld, st, tw);
     __syncthreads();
     const float2 *X = reinterpret_cast<const float2 *>(eng2::dyn_smem());
     constexpr int RL = eng2::row_ld(C::M);
     constexpr int F = C::F, N1 = C::N1, N2 = C::N2;
-    constexpr int PAIRS = (F - 1) * N1;
+    // bins below n_fft / 2 = N only need l1 < N1 / 2 (bin 2k + 1 with k < N / 2 reads
+    // X(k + 1) <= X(N / 2), which the transform still produced)
+    const int lg1 = ep.bin_hi < (int64_t)C::N ? C::LOGN1 - 1 : C::LOGN1;
+    const int PAIRS = (F - 1) << lg1;
     constexpr float Q = 0.78539816339744831f;   // pi / 4
     const int l2_0 = blockIdx.x * (F - 1);
     const int lane = threadIdx.x & 31;
@@ -400,7 +476,7 @@ k_pass2_ib(ScratchLoadIB<Cfg2<LOGN, 2, TS>> ld, SearchEpi2<Cfg2<LOGN, 2, TS>, fa
 #pragma unroll 1
     for (int p0 = 0; p0 < PAIRS; p0 += C::THREADS) {
         const int pr = p0 + (int)threadIdx.x;
-        const int f = pr / N1, l1 = pr - f * N1;
+        const int f = pr >> lg1, l1 = pr & ((1 << lg1) - 1);
         const int l2 = l2_0 + f;
         const bool own = pr < PAIRS && l2 < N2;
         float Fe = 0.f, Fo = 0.f;

@@ -158,10 +158,23 @@ int launch_interbin(const Plan &p, int band_idx, const BandDev &b, int64_t s0, i
     if (!attr1) { set_smem(k1, C1::SMEM); attr1 = true; }
     k1<<<dim3(C1::TILES, (unsigned)nc), C1::THREADS, C1::SMEM, s>>>(ld1, st1, tw->in2_f);
     if (mid) record_timing_event(mid, s);
+    if (p.tma) {   // 128-thread row tiles staged by bulk copies (8-byte mbarrier after the smem)
+        using D2 = Cfg2<LOGN, 2, 128>;
+        ScratchLoadIBTMA<D2> ld2{};
+        ld2.scratch = reinterpret_cast<const float2 *>(cb.scratch);
+        ld2.pf_dist = 2 * p.pf_dist;
+        ld2.err = p.qerr;
+        const auto ep = make_epi<LOGN, false, 128>(p, band_idx, b, c0, s0, cb);
+        auto k2 = k_pass2_ib<LOGN, 128, ScratchLoadIBTMA<D2>>;
+        static bool attr2t = false;
+        if (!attr2t) { set_smem(k2, D2::SMEM + 16); attr2t = true; }
+        k2<<<dim3(IBGeom<LOGN, 128>::TILES, (unsigned)nc), D2::THREADS, D2::SMEM + 16, s>>>(ld2, ep, tw->in1_f);
+        return 2;
+    }
     ScratchLoadIB<C2> ld2{};
     ld2.scratch = reinterpret_cast<const float2 *>(cb.scratch);
     const auto ep = make_epi<LOGN, false>(p, band_idx, b, c0, s0, cb);
-    auto k2 = k_pass2_ib<LOGN>;
+    auto k2 = k_pass2_ib<LOGN, 256, ScratchLoadIB<C2>>;
     static bool attr2 = false;
     if (!attr2) { set_smem(k2, C2::SMEM); attr2 = true; }
     k2<<<dim3(IBGeom<LOGN>::TILES, (unsigned)nc), C2::THREADS, C2::SMEM, s>>>(ld2, ep, tw->in1_f);
