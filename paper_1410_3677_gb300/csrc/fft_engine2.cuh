@@ -198,6 +198,11 @@ __device__ __forceinline__ unsigned char *dyn_smem() {
     return smem_raw;
 }
 
+template <class ST, class = void>
+struct StoreEarly { static constexpr bool value = false; };
+template <class ST>
+struct StoreEarly<ST, decltype(void(ST::kStoreEarly))> { static constexpr bool value = ST::kStoreEarly; };
+
 template <class LD, class = void>
 struct LoaderStaged { static constexpr bool value = false; };
 template <class LD>
@@ -284,9 +289,13 @@ __device__ __forceinline__ void run_pass(LD &ld, ST &st, const T *__restrict__ t
                 xr[r] = a; xi[r] = b;
             }
             dft<R1, DIR>(xr, xi);
+            // a store that touches no shared memory can take each job as it is done
+            if constexpr (StoreEarly<ST>::value) st.template store<R1, R0>(q, xr, xi);
         }
+        if constexpr (!StoreEarly<ST>::value) {
 #pragma unroll
-        for (int i = 0; i < NJ1; ++i) st.template store<R1, R0>(job<MAPM, SEQ, TPF, THREADS>(i), &re[i * R1], &im[i * R1]);
+            for (int i = 0; i < NJ1; ++i) st.template store<R1, R0>(job<MAPM, SEQ, TPF, THREADS>(i), &re[i * R1], &im[i * R1]);
+        }
     }
 }
 

@@ -85,37 +85,54 @@ struct SearchLoad2 {
     }
 };
 
-// Pass 1 output: twiddle W_N^{k1 l2}, l2 = j + r JPF, as W^{k1 j} (W^{k1 JPF})^r
-// (two lookups W_N^m = hi[m >> log N1] lo[m & (N1 - 1)] per job), then the
-// transposed store A_t[l2][k1] into the cell's scratch slot.  Scratch is written
-// and read through L2 only (st.global.cg / ld.global.cg): it is streamed once
-// each way, and a slot reused within one launch never meets a stale L1 line.
+// The four-step twiddle W_N^{k1 l2} between the passes, applied by the pass-2
+// loaders to the elements k1 = j + r JPF of row l2 as W^{l2 j} (W^{l2 JPF})^r,
+// the two factors from the tables W_N^m = hi[m >> log N1] lo[m & (N1 - 1)].
+// Pass 1 is bound by instruction issue and pass 2 by its DRAM reads, so the
+// multiplies sit in the pass that has issue slots to spare.
+template <int LOGN1>
+struct InterTw {
+    const float *lo, *hi;
+    __device__ __forceinline__ float2 wn(int m) const {
+        const float2 th = __ldg(reinterpret_cast<const float2 *>(hi) + (m >> LOGN1));
+        const float2 tl = __ldg(reinterpret_cast<const float2 *>(lo) + (m & ((1 << LOGN1) - 1)));
+        return float2{th.x * tl.x - th.y * tl.y, th.x * tl.y + th.y * tl.x};
+    }
+    template <int R, int JPF>
+    __device__ __forceinline__ void apply(int l2, int j, float *re, float *im) const {
+        float2 w = wn(l2 * j);
+        const float2 st = wn(l2 * JPF);
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const float xr = re[r], xi = im[r];
+            re[r] = xr * w.x - xi * w.y;
+            im[r] = xr * w.y + xi * w.x;
+            if (r + 1 < R) w = float2{w.x * st.x - w.y * st.y, w.x * st.y + w.y * st.x};
+        }
+    }
+};
+
+// Pass 1 output: the transposed store A_t[l2][k1], l2 = j + r JPF, into the
+// cell's scratch slot.  Scratch is written and read through L2 only
+// (st.global.cg / ld.global.cg): it is streamed once each way, and a slot reused
+// within one launch never meets a stale L1 line.
 template <class C>
 struct ScratchStore2 {
+    static constexpr bool kStoreEarly = true;
     float2 *scratch;
-    const float *lo, *hi;
     float2 *base;
     int k1_0;
     __device__ void init(int tile, int64_t, int64_t slot) {
         base = scratch + slot * 2 * C::N;
         k1_0 = tile * C::F;
     }
-    __device__ __forceinline__ float2 wn(int m) const {
-        const float2 th = __ldg(reinterpret_cast<const float2 *>(hi) + (m >> C::LOGN1));
-        const float2 tl = __ldg(reinterpret_cast<const float2 *>(lo) + (m & (C::N1 - 1)));
-        return float2{th.x * tl.x - th.y * tl.y, th.x * tl.y + th.y * tl.x};
-    }
     template <int R, int JPF>
     __device__ __forceinline__ void store(const eng2::Job &q, float *re, float *im) const {
-        const int k1 = k1_0 + q.f;
-        float2 w = wn(k1 * q.j);
-        const float2 st = wn(k1 * JPF);
-        float2 *dst = base + (int64_t)q.t * C::N + (int64_t)q.j * C::N1 + k1;
+        float2 *dst = base + (int64_t)q.t * C::N + (int64_t)q.j * C::N1 + k1_0 + q.f;
 #pragma unroll
         for (int r = 0; r < R; ++r) {
-            const float xr = re[r], xi = im[r];
-            __stcg(dst + (int64_t)r * JPF * C::N1, float2{xr * w.x - xi * w.y, xr * w.y + xi * w.x});
-            if (r + 1 < R) w = float2{w.x * st.x - w.y * st.y, w.x * st.y + w.y * st.x};
+            __stcg(dst, float2{re[r], im[r]});
+            dst += JPF * C::N1;
         }
     }
 };
@@ -125,6 +142,7 @@ template <class C>
 struct ScratchLoad2 {
     const float2 *scratch;
     int64_t pf_dist;     // two-launch form: prefetch the tile this many CTAs ahead (0: off)
+    InterTw<C::LOGN1> tw;
     const float2 *base;
     int l2_0;
     __device__ void init(int tile, int64_t, int64_t slot) {
@@ -154,6 +172,7 @@ struct ScratchLoad2 {
             const float2 v = __ldcg(row + r * JPF);
             re[r] = v.x; im[r] = v.y;
         }
+        tw.template apply<R, JPF>(l2_0 + q.f, q.j, re, im);
     }
 };
 
@@ -170,11 +189,14 @@ struct ScratchLoadTMA {
     const float2 *scratch;
     int64_t pf_dist;        // see ScratchLoad2::prefetch_ahead
     uint32_t *err;          // set when the copy does not complete within 1 s
+    InterTw<C::LOGN1> tw;
+    int l2_0;
     const float2 *src;
     const float2 *rows;     // staged rows in shared memory: [t F + f][N1]
     uint64_t *bar;
     __device__ void init(int tile, int64_t, int64_t slot) {
         src = scratch + slot * 2 * C::N + (int64_t)tile * C::F * C::N1;
+        l2_0 = tile * C::F;
         unsigned char *sm = eng2::dyn_smem();
         rows = reinterpret_cast<const float2 *>(sm);
         bar = reinterpret_cast<uint64_t *>(sm + C::SMEM);
@@ -223,6 +245,7 @@ struct ScratchLoadTMA {
             const float2 v = row[r * JPF];
             re[r] = v.x; im[r] = v.y;
         }
+        tw.template apply<R, JPF>(l2_0 + q.f, q.j, re, im);
     }
 };
 
@@ -336,6 +359,7 @@ __global__ void __launch_bounds__(TS, 768 / TS) k_pass2(LD ld, ST st, const floa
 template <class C>
 struct ScratchLoadIB {
     const float2 *scratch;
+    InterTw<C::LOGN1> tw;
     const float2 *base;
     int l2_0;
     __device__ void init(int tile, int64_t, int64_t slot) {
@@ -351,6 +375,7 @@ struct ScratchLoadIB {
             const float2 v = __ldcg(row + r * JPF);
             re[r] = v.x; im[r] = v.y;
         }
+        tw.template apply<R, JPF>(l2, q.j, re, im);
     }
 };
 
@@ -363,6 +388,7 @@ struct ScratchLoadIBTMA {
     const float2 *scratch;
     int64_t pf_dist;
     uint32_t *err;
+    InterTw<C::LOGN1> tw;
     const float2 *base;
     const float2 *rows;
     uint64_t *bar;
@@ -424,6 +450,7 @@ struct ScratchLoadIBTMA {
             const float2 v = row[r * JPF];
             re[r] = v.x; im[r] = v.y;
         }
+        tw.template apply<R, JPF>((l2_0 + q.f) & (C::N2 - 1), q.j, re, im);
     }
 };
 

@@ -56,12 +56,14 @@ int launch_two(const Plan &p, int band_idx, const BandDev &b, int64_t s0, int64_
     if (p.tma && p.p2_threads == 128) {   // smaller tiles, six CTAs per SM
         ScratchLoadTMA<Cfg2<LOGN, 2, 128>> lt{};
         lt.scratch = ld2.scratch;
+        lt.tw = ld2.tw;
         lt.pf_dist = 2 * ld2.pf_dist;
         lt.err = p.qerr;
         launch_pass2<LOGN, LOWER, 128>(p, band_idx, b, s0, c0, nc, s, cb, lt, tw, 16);
     } else if (p.tma) {   // rows staged by bulk copies; an 8-byte mbarrier after the shared memory
         ScratchLoadTMA<C2> lt{};
         lt.scratch = ld2.scratch;
+        lt.tw = ld2.tw;
         lt.pf_dist = ld2.pf_dist;
         lt.err = p.qerr;
         launch_pass2<LOGN, LOWER, 256>(p, band_idx, b, s0, c0, nc, s, cb, lt, tw, 16);
@@ -118,10 +120,9 @@ int launch_search2(const Plan &p, int band_idx, const BandDev &b, int64_t s0, in
     ld1.s0 = s0;
     ScratchStore2<C1> st1{};
     st1.scratch = reinterpret_cast<float2 *>(cb.scratch);
-    st1.lo = tw->lo_f;
-    st1.hi = tw->hi_f;
     ScratchLoad2<C2> ld2{};
     ld2.scratch = reinterpret_cast<const float2 *>(cb.scratch);
+    ld2.tw = {tw->lo_f, tw->hi_f};
     ld2.pf_dist = p.pf_dist;
     const bool lower = b.hi < (int64_t)C2::N / 2;
     if (fused_supported(p, LOGN) && cb.ctl) {
@@ -151,8 +152,6 @@ int launch_interbin(const Plan &p, int band_idx, const BandDev &b, int64_t s0, i
     ld1.s0 = s0;
     ScratchStore2<C1> st1{};
     st1.scratch = reinterpret_cast<float2 *>(cb.scratch);
-    st1.lo = tw->lo_f;
-    st1.hi = tw->hi_f;
     auto k1 = k_pass2<LOGN, 1, eng2::kMapFJ, SearchLoad2<C1>, ScratchStore2<C1>, 256, false>;
     static bool attr1 = false;
     if (!attr1) { set_smem(k1, C1::SMEM); attr1 = true; }
@@ -162,6 +161,7 @@ int launch_interbin(const Plan &p, int band_idx, const BandDev &b, int64_t s0, i
         using D2 = Cfg2<LOGN, 2, 128>;
         ScratchLoadIBTMA<D2> ld2{};
         ld2.scratch = reinterpret_cast<const float2 *>(cb.scratch);
+        ld2.tw = {tw->lo_f, tw->hi_f};
         ld2.pf_dist = 2 * p.pf_dist;
         ld2.err = p.qerr;
         const auto ep = make_epi<LOGN, false, 128>(p, band_idx, b, c0, s0, cb);
@@ -173,6 +173,7 @@ int launch_interbin(const Plan &p, int band_idx, const BandDev &b, int64_t s0, i
     }
     ScratchLoadIB<C2> ld2{};
     ld2.scratch = reinterpret_cast<const float2 *>(cb.scratch);
+    ld2.tw = {tw->lo_f, tw->hi_f};
     const auto ep = make_epi<LOGN, false>(p, band_idx, b, c0, s0, cb);
     auto k2 = k_pass2_ib<LOGN, 256, ScratchLoadIB<C2>>;
     static bool attr2 = false;
