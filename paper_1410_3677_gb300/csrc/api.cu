@@ -320,7 +320,8 @@ void create_impl(Plan &p, const fstat_plan_desc *d) {
         p.wbuf[q] = dalloc<unsigned char>(p, (size_t)p.sky_batch * p.w_stride * w_elem, n_alloc);
         check(cudaMemsetAsync(p.wbuf[q], 0, (size_t)p.sky_batch * p.w_stride * w_elem, s), "memset");
     }
-    p.dbuf = dalloc<double>(p, (size_t)p.sky_batch * p.n_max, n_alloc);
+    // per-sample delays (FP64 form) or 16-byte shift records (FP32 form)
+    p.dbuf = dalloc<double>(p, (size_t)p.sky_batch * p.n_max * (fp32 ? 2 : 1), n_alloc);
     p.partials = dalloc<double>(p, std::max<int64_t>((int64_t)p.sky_batch * nblk * 3, 256), n_alloc);
     p.S = dalloc<double>(p, 3 * p.sky_batch, n_alloc);
     for (int q = 0; q < 2; ++q) p.normbuf[q] = dalloc<double>(p, 4 * p.sky_batch, n_alloc);

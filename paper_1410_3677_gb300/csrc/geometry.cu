@@ -88,9 +88,20 @@ __global__ void k_sigma2_final(const double *__restrict__ partials, int nblk, in
 }
 
 // ------------------------------------------------------------------ geometry
+// FP32 form: the delay of sample j reduced once, in FP64, to the sample shift
+// d_j / dt = I + phi (integer part exact, fraction in FP32) and to the
+// band-offset phase f_off d_j mod 1 with its increment f_off (d_{j+1} - d_j), so
+// that the detector-time inversion and the phase interpolation run in integer
+// and FP32 arithmetic (positions and phases to ~1e-7 samples and cycles).
+struct DelayRec {
+    int I;
+    float phi, psi, dpsi;
+};
+
 struct GeoArgs {
     const double *r;
     const double *d;          // per-sample delays of the sky batch, [sky][stride]
+    const DelayRec *dr;       // FP32 form: the same as shift records
     int64_t d_stride;
     const void *xu;
     int64_t m_up;
@@ -136,30 +147,133 @@ __global__ void __launch_bounds__(256) k_delays(const double *__restrict__ r,
     if (k < n) d[(int64_t)sl * stride + k] = delay_at(r, sky[s0 + sl], k);
 }
 
+// Shift records of every sample of skies [s0, s0 + gridDim.y); d_{k+1} comes
+// from the next lane (the last lane of a warp evaluates it).  The increment of
+// the last sample is never used (the interpolation segment index is <= n - 2).
+__global__ void __launch_bounds__(256) k_delays_split(const double *__restrict__ r,
+                                                      const SkyConst *__restrict__ sky, int64_t s0,
+                                                      int64_t n, int64_t stride, double inv_dt,
+                                                      double f_off, DelayRec *__restrict__ out) {
+    const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int sl = blockIdx.y;
+    __shared__ double dsh[257];
+    const SkyConst sc = sky[s0 + sl];
+    const double dk = k < n ? delay_at(r, sc, k) : 0.0;
+    DelayRec o;
+    const double sh = dk * inv_dt;
+    const double fl = floor(sh);
+    o.I = (int)fl;
+    o.phi = (float)(sh - fl);
+    o.psi = 0.f;
+    o.dpsi = 0.f;
+    if (f_off != 0.0) {   // uniform: no phase records for a band at zero offset
+        dsh[threadIdx.x] = dk;
+        if (threadIdx.x == 0) {
+            const int64_t kn = k + blockDim.x;
+            dsh[blockDim.x] = kn < n ? delay_at(r, sc, kn) : 0.0;
+        }
+        __syncthreads();
+        const double cyc = f_off * dk;
+        o.psi = (float)(cyc - floor(cyc));
+        if (k + 1 < n) o.dpsi = (float)(f_off * (dsh[threadIdx.x + 1] - dk));
+    }
+    if (k < n) out[(int64_t)sl * stride + k] = o;
+}
+
 template <bool FP32>
 __global__ void __launch_bounds__(256) k_geometry(GeoArgs g) {
     __shared__ double sh[8];
     const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const int sl = blockIdx.y;
-    const SkyConst sc = g.sky[g.s0 + sl];
     double saa = 0.0, sbb = 0.0, sab = 0.0;    // FP64 form
     float saa_f = 0.f, sbb_f = 0.f, sab_f = 0.f;   // FP32 form
-    if (k < g.n) {
-        // detector time t of barycentric sample k: t = k dt - d(k dt - d(k dt))
+    if constexpr (FP32) {
+        // the sky's constants in FP32, converted once per block
+        __shared__ float cf[12];
+        if (threadIdx.x < 12) {
+            const SkyConst &sc = g.sky[g.s0 + sl];
+            const int i = threadIdx.x;
+            cf[i] = i < 5 ? (float)sc.A[i] : i < 9 ? (float)sc.B[i - 5]
+                  : i == 9 ? (float)(sc.alpha - g.phi0) : i == 10 ? (float)g.dt : 0.f;
+        }
+        __syncthreads();
+        if (k < g.n) {
+            // detector time t of barycentric sample k, t = k dt - d(k dt - d(k dt)),
+            // as u = t / dt = A - F1: A an exact integer, F1 an FP32 fraction
+            const int n = (int)g.n, kk = (int)k;
+            const DelayRec *dr = g.dr + (int64_t)sl * g.d_stride;
+            const DelayRec rk = dr[kk];
+            const int a0 = kk - rk.I;                       // u0 = a0 - phi_k
+            const int j0 = min(max(a0 - 1, 0), n - 2);
+            const float f0 = (float)(a0 - j0) - rk.phi;     // u0 - j0
+            const DelayRec p0 = dr[j0], p1 = dr[j0 + 1];
+            const float F1 = p0.phi + f0 * ((float)(p1.I - p0.I) + (p1.phi - p0.phi));
+            const int A = kk - p0.I;
+            const float fl1 = floorf(-F1);
+            int j = A + (int)fl1;
+            float f = -F1 - fl1;                            // u - j in [0, 1)
+            const int jc = min(max(j, 0), n - 2);
+            f += (float)(j - jc);
+            j = jc;
+            const bool valid = F1 <= (float)A && F1 >= (float)(A - (n - 1));
+            // band-offset phase at t, cycles: psi_j + f dpsi_j (mod 1)
+            const DelayRec q0 = dr[j];
+            const float cyc = q0.psi + f * q0.dpsi;
+            const float frs = cyc - rintf(cyc);
+            // hour angle h = alpha - phi0 - Omega_r t (|h| < 20 rad, error ~1e-6 rad
+            // from t rounded to FP32)
+            const float uf = (float)A - F1;
+            const float hr = cf[9] - (float)kOmegaR * (uf * cf[10]);
+            float s1, c1;
+            sincosf(hr, &s1, &c1);
+            const float c2 = c1 * c1 - s1 * s1, s2 = 2.f * s1 * c1;
+            const float av = cf[0] * c2 + cf[1] * s2 + cf[2] * c1 + cf[3] * s1 + cf[4];
+            const float bv = cf[5] * c2 + cf[6] * s2 + cf[7] * c1 + cf[8] * s1;
+            float yr = 0.f, yi = 0.f;
+            if (valid) {
+                // Keys cubic (a = -1/2) at p = U u = U A - U F1 on the upsampled series,
+                // periodic indexing (only tap -1 and taps >= U n wrap, a single step)
+                const float up = -(float)g.U * F1;
+                const float upf = floorf(up);
+                const float mu = up - upf;
+                const int64_t i0 = (int64_t)g.U * A + (int64_t)upf - 1;
+                const float w0 = ((-0.5f * mu + 1.f) * mu - 0.5f) * mu;
+                const float w1 = (1.5f * mu - 2.5f) * mu * mu + 1.f;
+                const float w2 = ((-1.5f * mu + 2.f) * mu + 0.5f) * mu;
+                const float w3 = (0.5f * mu - 0.5f) * mu * mu;
+                const float *xu = (const float *)g.xu;
+                float x4[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int64_t v = i0 + q;
+                    x4[q] = xu[v < 0 ? v + g.m_up : (v >= g.m_up ? v - g.m_up : v)];
+                }
+                const float v = w0 * x4[0] + w1 * x4[1] + w2 * x4[2] + w3 * x4[3];
+                float sp, cp;
+                sincospif(2.f * frs, &sp, &cp);
+                yr = v * cp;
+                yi = -v * sp;
+                saa_f = av * av;
+                sbb_f = bv * bv;
+                sab_f = av * bv;
+            }
+            float4 *w = (float4 *)g.w + (int64_t)sl * g.w_stride;
+            w[k] = make_float4(yr * av, yi * av, yr * bv, yi * bv);
+            if (g.dbg_y) {
+                g.dbg_y[2 * k] = yr; g.dbg_y[2 * k + 1] = yi;
+                g.dbg_a[k] = av; g.dbg_b[k] = bv; g.dbg_mask[k] = valid;
+            }
+        }
+    } else if (k < g.n) {
+        const SkyConst sc = g.sky[g.s0 + sl];
+        // detector time t of barycentric sample k: t = k dt - d(k dt - d(k dt)),
+        // in the oracle's rounding sequence, for 1e-10 agreement of F
         const double *dd = g.d + (int64_t)sl * g.d_stride;
         const double dk = dd[k];
-        double u0, d1, u, d2;
-        if constexpr (FP32) {     // reciprocal multiply: positions to ~1e-11 samples
-            u0 = (double)k - dk * g.inv_dt;
-            d1 = delay_lin(dd, g.n, u0);
-            u = (double)k - d1 * g.inv_dt;
-            d2 = delay_lin(dd, g.n, u);
-        } else {                  // the oracle's rounding sequence, for 1e-10 agreement of F
-            u0 = __dsub_rn((double)k, __ddiv_rn(dk, g.dt));
-            d1 = delay_lin(dd, g.n, u0);
-            u = __dsub_rn((double)k, __ddiv_rn(d1, g.dt));
-            d2 = delay_lin(dd, g.n, u);
-        }
+        const double u0 = __dsub_rn((double)k, __ddiv_rn(dk, g.dt));
+        const double d1 = delay_lin(dd, g.n, u0);
+        const double u = __dsub_rn((double)k, __ddiv_rn(d1, g.dt));
+        const double d2 = delay_lin(dd, g.n, u);
         const bool valid = (u >= 0.0) && (u <= (double)(g.n - 1));
         // Keys cubic (a = -1/2) on the upsampled series, periodic indexing
         const double p = (double)g.U * u;
@@ -178,42 +292,7 @@ __global__ void __launch_bounds__(256) k_geometry(GeoArgs g) {
         // band-offset phase, cycles, reduced in FP64
         const double cyc = __dmul_rn(g.f_off, d2);
         const double fr = __dsub_rn(cyc, floor(cyc));
-        if constexpr (FP32) {
-            // hour angle h = alpha - phi0 - Omega_r t in FP32 (|h| < 20 rad, error
-            // ~1e-6 rad from t = u dt rounded to FP32)
-            const float hr = (float)(sc.alpha - g.phi0) - (float)kOmegaR * ((float)u * (float)g.dt);
-            float s1, c1;
-            sincosf(hr, &s1, &c1);
-            const float c2 = c1 * c1 - s1 * s1, s2 = 2.f * s1 * c1;
-            const float av = (float)sc.A[0] * c2 + (float)sc.A[1] * s2 + (float)sc.A[2] * c1 +
-                             (float)sc.A[3] * s1 + (float)sc.A[4];
-            const float bv = (float)sc.B[0] * c2 + (float)sc.B[1] * s2 + (float)sc.B[2] * c1 +
-                             (float)sc.B[3] * s1;
-            float yr = 0.f, yi = 0.f;
-            if (valid) {
-                const float mu = (float)(p - pf);
-                const float w0 = ((-0.5f * mu + 1.f) * mu - 0.5f) * mu;
-                const float w1 = (1.5f * mu - 2.5f) * mu * mu + 1.f;
-                const float w2 = ((-1.5f * mu + 2.f) * mu + 0.5f) * mu;
-                const float w3 = (0.5f * mu - 0.5f) * mu * mu;
-                const float *xu = (const float *)g.xu;
-                const float v = w0 * xu[idx[0]] + w1 * xu[idx[1]] + w2 * xu[idx[2]] + w3 * xu[idx[3]];
-                const float frs = (float)(fr - rint(fr));
-                float sp, cp;
-                sincospif(2.f * frs, &sp, &cp);
-                yr = v * cp;
-                yi = -v * sp;
-                saa_f = av * av;
-                sbb_f = bv * bv;
-                sab_f = av * bv;
-            }
-            float4 *w = (float4 *)g.w + (int64_t)sl * g.w_stride;
-            w[k] = make_float4(yr * av, yi * av, yr * bv, yi * bv);
-            if (g.dbg_y) {
-                g.dbg_y[2 * k] = yr; g.dbg_y[2 * k + 1] = yi;
-                g.dbg_a[k] = av; g.dbg_b[k] = bv; g.dbg_mask[k] = valid;
-            }
-        } else {
+        {
             const double h = sc.alpha - (g.phi0 + kOmegaR * (u * g.dt));
             double s1, c1;
             sincos(h, &s1, &c1);
@@ -459,6 +538,7 @@ int launch_geometry(const Plan &p, const BandDev &b, int64_t s0, int64_t ns, boo
     GeoArgs g;
     g.r = b.r;
     g.d = p.dbuf;
+    g.dr = reinterpret_cast<const DelayRec *>(p.dbuf);
     g.d_stride = p.n_max;
     g.xu = b.xu;
     g.U = p.desc.upsample;
@@ -479,9 +559,14 @@ int launch_geometry(const Plan &p, const BandDev &b, int64_t s0, int64_t ns, boo
     g.dbg_b = dbg_b;
     g.dbg_mask = dbg_mask;
     dim3 grid(g.nblk, (unsigned)ns);
-    k_delays<<<grid, 256, 0, s>>>(b.r, p.sky, s0, b.n, p.n_max, p.dbuf);
-    if (fp32) k_geometry<true><<<grid, 256, 0, s>>>(g);
-    else k_geometry<false><<<grid, 256, 0, s>>>(g);
+    if (fp32) {
+        k_delays_split<<<grid, 256, 0, s>>>(b.r, p.sky, s0, b.n, p.n_max, g.inv_dt, b.f_off,
+                                            reinterpret_cast<DelayRec *>(p.dbuf));
+        k_geometry<true><<<grid, 256, 0, s>>>(g);
+    } else {
+        k_delays<<<grid, 256, 0, s>>>(b.r, p.sky, s0, b.n, p.n_max, p.dbuf);
+        k_geometry<false><<<grid, 256, 0, s>>>(g);
+    }
     return 2;
 }
 
