@@ -153,6 +153,19 @@ typedef struct fstat_plan fstat_plan;
    2^32 - 1 cells), FSTAT_ERR_OOM, FSTAT_ERR_CUDA. */
 fstat_status fstat_plan_create(fstat_plan **out, const fstat_plan_desc *desc);
 
+/* Replace the data of band `band` (0-based) by the next segment of the same
+   shape (Sect. 2: the search runs over many frames of one band): n, dt and n_fft
+   must equal the plan's band; x or x32, r, f_off, phi0 and eps are taken.  The
+   arrays are read from host or device memory as desc->inputs_on_device said and
+   are copied before the call returns; the next fstat_search recomputes the
+   noise variance and the upsample from them.  Device memory is reused: a
+   stream of segments pays the allocation of fstat_plan_create once.  Earlier
+   candidates stay readable until the next search.  Errors: FSTAT_ERR_ARG (band
+   out of range, another shape, non-finite f_off or phi0, not exactly one of
+   x, x32, r NULL), FSTAT_ERR_OOM (the float32 staging buffer), FSTAT_ERR_CUDA,
+   FSTAT_ERR_STATE (poisoned plan). */
+fstat_status fstat_plan_set_band(fstat_plan *plan, int band, const fstat_band *data);
+
 /* Search cells [cell_begin, cell_end) in the order cell = (band * n_sky + sky)
    * n_spin + spin (cell_end = -1: to the last cell), replacing the candidates of
    the previous call.  Runs the whole hot path from the raw series: per band the

@@ -266,9 +266,9 @@ void create_impl(Plan &p, const fstat_plan_desc *d) {
         if (hb.x) {
             copy_in(b.x, hb.x, b.n * sizeof(double), dev, s);
         } else {
-            float *tmp = dalloc<float>(p, b.n, n_alloc);
-            copy_in(tmp, hb.x32, b.n * sizeof(float), dev, s);
-            k_f32_to_f64<<<(unsigned)((b.n + 255) / 256), 256, 0, s>>>(tmp, b.n, b.x);
+            b.x32 = dalloc<float>(p, b.n, n_alloc);
+            copy_in(b.x32, hb.x32, b.n * sizeof(float), dev, s);
+            k_f32_to_f64<<<(unsigned)((b.n + 255) / 256), 256, 0, s>>>(b.x32, b.n, b.x);
             ++p.launches;
         }
         copy_in(b.r, hb.r, 3 * b.n * sizeof(double), dev, s);
@@ -433,6 +433,16 @@ void free_all(Plan &p) {
     if (p.own_stream && p.stream) cudaStreamDestroy(p.stream);
     p.stream = nullptr;
     p.own_stream = false;
+    if (p.h_rec) cudaFreeHost(p.h_rec);
+    if (p.h_tmp) cudaFreeHost(p.h_tmp);
+    p.h_rec = p.h_tmp = nullptr;
+    p.h_rec_cap = 0;
+    if (p.cand_tmp) cudaFree(p.cand_tmp);
+    if (p.sort_hist) cudaFree(p.sort_hist);
+    p.cand_tmp = nullptr;
+    p.sort_hist = nullptr;
+    p.sort_cap = 0;
+    p.cand_sorted = nullptr;
 }
 
 // ---------------------------------------------------------------- sampled timing
@@ -500,6 +510,8 @@ void band_prologue(Plan &p, BandDev &b) {
 }
 
 void enqueue_search(Plan &p, int64_t begin, int64_t end) {
+    p.cand_begin = begin;
+    p.cand_end = end;
     const fstat_plan_desc &d = p.desc;
     const bool fp32 = d.form == FSTAT_FP32_BATCHED;
     cudaStream_t s = p.stream;
@@ -642,6 +654,7 @@ void finish_search(Plan &p, bool recycle_events) {
     check(cudaMemcpy(&cnt, p.cand_count, sizeof(cnt), cudaMemcpyDeviceToHost), "count");
     p.last_total = (int64_t)cnt;
     p.searched = true;
+    p.cand_sorted = nullptr;
 }
 
 void drop_graph(Plan &p) {
@@ -750,6 +763,8 @@ using namespace fstat;
 namespace {
 
 inline uint64_t cand_key(const fstat::CandRecord &r) { return ((uint64_t)r.cell << 32) | r.bin; }
+constexpr int64_t kDeviceSortMin = 1 << 16;   // fewer records are sorted on the host
+constexpr int64_t kTileSlack = 4096;          // device positions are 32-bit
 
 // Runs f(t) for t in [0, nt) on nt threads (the calling thread takes t = 0).
 template <class Fn>
@@ -917,11 +932,56 @@ fstat_status fstat_candidates_get(fstat_plan *p, fstat_candidate *buf, int64_t c
         if (n_total) *n_total = p->last_total;
         if (cap == 0) return p->last_total > 0 ? FSTAT_ERR_OVERFLOW : FSTAT_OK;   // count only
         const int64_t kept = std::min<int64_t>(p->last_total, p->cand_capacity);
-        std::unique_ptr<CandRecord[]> rec(new CandRecord[(size_t)std::max<int64_t>(kept, 1)]);
-        std::unique_ptr<CandRecord[]> tmp(new CandRecord[(size_t)std::max<int64_t>(kept, 1)]);
-        if (kept > 0)
-            check(cudaMemcpy(rec.get(), p->cand, kept * sizeof(CandRecord), cudaMemcpyDeviceToHost), "candidates");
-        const CandRecord *sorted = sort_records(rec.get(), tmp.get(), kept);
+        if (kept > p->h_rec_cap) {   // pinned staging, reused: no page faults, full-rate copies
+            if (p->h_rec) cudaFreeHost(p->h_rec);
+            if (p->h_tmp) cudaFreeHost(p->h_tmp);
+            p->h_rec = p->h_tmp = nullptr;
+            p->h_rec_cap = 0;
+            const int64_t want = std::max<int64_t>(kept, kept + kept / 4);
+            if (cudaHostAlloc((void **)&p->h_rec, want * sizeof(CandRecord), cudaHostAllocDefault) != cudaSuccess ||
+                cudaHostAlloc((void **)&p->h_tmp, want * sizeof(CandRecord), cudaHostAllocDefault) != cudaSuccess) {
+                cudaGetLastError();
+                if (p->h_rec) cudaFreeHost(p->h_rec);
+                p->h_rec = p->h_tmp = nullptr;
+                throw std::bad_alloc();
+            }
+            p->h_rec_cap = want;
+        }
+        CandRecord *rec = p->h_rec, *tmp = p->h_tmp;
+        // many records: sorted on the device once per search, then read back in order
+        const bool dev_sort = kept >= kDeviceSortMin && kept < (int64_t(1) << 32) - kTileSlack;
+        if (dev_sort && !p->cand_sorted) {
+            if (kept > p->sort_cap) {
+                if (p->cand_tmp) cudaFree(p->cand_tmp);
+                if (p->sort_hist) cudaFree(p->sort_hist);
+                p->cand_tmp = nullptr;
+                p->sort_hist = nullptr;
+                p->sort_cap = 0;
+                const int64_t want = std::min<int64_t>(p->cand_capacity, kept + kept / 4);
+                const int64_t nblk = (want + 4095) / 4096;
+                if (cudaMalloc((void **)&p->cand_tmp, want * sizeof(CandRecord)) != cudaSuccess ||
+                    cudaMalloc((void **)&p->sort_hist, 256 * nblk * sizeof(uint32_t)) != cudaSuccess) {
+                    cudaGetLastError();
+                    if (p->cand_tmp) cudaFree(p->cand_tmp);
+                    p->cand_tmp = nullptr;
+                    throw OomError{};
+                }
+                p->sort_cap = want;
+            }
+            int bin_bits = 0;
+            while ((int64_t(1) << bin_bits) < p->n_fft_max) ++bin_bits;
+            p->cand_sorted = launch_cand_sort(p->cand, p->cand_tmp, p->sort_hist, kept, (uint32_t)p->cand_begin,
+                                              (uint64_t)(p->cand_end - p->cand_begin), bin_bits, p->stream,
+                                              &p->launches);
+            check(cudaGetLastError(), "candidate sort");
+        }
+        if (kept > 0) {
+            check(cudaMemcpyAsync(rec, dev_sort ? p->cand_sorted : p->cand, kept * sizeof(CandRecord),
+                                  cudaMemcpyDeviceToHost, p->stream),
+                  "candidates");
+            check(cudaStreamSynchronize(p->stream), "candidates");
+        }
+        const CandRecord *sorted = kept > 0 && !dev_sort ? sort_records(rec, tmp, kept) : rec;
         const int64_t nw = std::min<int64_t>(kept, cap);
         const fstat_plan_desc &d = p->desc;
         const int64_t per_band = d.n_sky * d.n_spin;
@@ -948,6 +1008,50 @@ fstat_status fstat_candidates_get(fstat_plan *p, fstat_candidate *buf, int64_t c
         });
         if (n_written) *n_written = nw;
         return p->last_total > nw ? FSTAT_ERR_OVERFLOW : FSTAT_OK;
+    });
+}
+
+fstat_status fstat_plan_set_band(fstat_plan *p, int band, const fstat_band *nb) {
+    return guarded(p, [&]() -> fstat_status {
+        if (!nb || band < 0 || band >= p->desc.n_bands) {
+            p->err = "band out of range";
+            return FSTAT_ERR_ARG;
+        }
+        BandDev &b = p->bands[(size_t)band];
+        int64_t nf = nb->n_fft;
+        if (nf == 0) { nf = 1; while (nf < 2 * nb->n) nf <<= 1; }
+        if (nb->n != b.n || nb->dt != b.dt || nf != b.n_fft) {
+            p->err = "n, dt and n_fft must equal those of the plan's band";
+            return FSTAT_ERR_ARG;
+        }
+        if (!is_finite(nb->f_off) || !is_finite(nb->phi0) || (nb->x == nullptr) == (nb->x32 == nullptr) || !nb->r) {
+            p->err = "bad f_off/phi0, or not exactly one of x, x32, or r is NULL";
+            return FSTAT_ERR_ARG;
+        }
+        const bool dev = p->desc.inputs_on_device == 1;
+        cudaStream_t s = p->stream;
+        if (nb->x) {
+            copy_in(b.x, nb->x, b.n * sizeof(double), dev, s);
+        } else {
+            if (!b.x32) {
+                int n_alloc = 0;
+                b.x32 = dalloc<float>(*p, b.n, n_alloc);
+            }
+            copy_in(b.x32, nb->x32, b.n * sizeof(float), dev, s);
+            k_f32_to_f64<<<(unsigned)((b.n + 255) / 256), 256, 0, s>>>(b.x32, b.n, b.x);
+            check(cudaGetLastError(), "launch");
+            ++p->launches;
+        }
+        copy_in(b.r, nb->r, 3 * b.n * sizeof(double), dev, s);
+        // scalars are kernel arguments of a captured search: a change forces a recapture
+        if (nb->f_off != b.f_off || nb->phi0 != b.phi0 || nb->eps != b.eps) {
+            b.f_off = nb->f_off;
+            b.phi0 = nb->phi0;
+            b.eps = nb->eps;
+            drop_graph(*p);
+        }
+        check(cudaStreamSynchronize(s), "band copy");
+        return FSTAT_OK;
     });
 }
 

@@ -57,6 +57,7 @@ struct BandDev {
     int logn = 0;
     int64_t lo = 0, hi = 0;
     double *x = nullptr;      // [n] float64 (converted from float32 when needed)
+    float *x32 = nullptr;     // [n] staging of a float32 series (allocated on first use)
     double *r = nullptr;      // [3n]
     double *sigma2 = nullptr; // device scalar
     void *xu = nullptr;       // [U n]: double (FP64 form) or float (FP32 form)
@@ -135,6 +136,18 @@ struct Plan {
     CandRecord *cand = nullptr;
     unsigned long long *cand_count = nullptr;
     int64_t cand_capacity = 0;
+    // pinned host staging of the candidate records (read back and sorted there),
+    // grown on demand and reused by later calls
+    CandRecord *h_rec = nullptr, *h_tmp = nullptr;
+    int64_t h_rec_cap = 0;
+    // device sort of the records before the read-back: the other ping-pong buffer,
+    // the digit counts, the cell range of the records and the sorted buffer (null
+    // until the first read-back after a search)
+    CandRecord *cand_tmp = nullptr;
+    uint32_t *sort_hist = nullptr;
+    int64_t sort_cap = 0;
+    int64_t cand_begin = 0, cand_end = 0;
+    const CandRecord *cand_sorted = nullptr;
     int64_t last_total = 0;
     bool searched = false;
 
@@ -216,6 +229,11 @@ int launch_geometry(const Plan &p, const BandDev &b, int64_t s0, int64_t ns, boo
 
 // Per-sky S sums and normalisations for the ns skies of the last geometry launch.
 int launch_reduce_norms(const Plan &p, const BandDev &b, int64_t ns, double *norm, cudaStream_t s);
+// Stable device sort of n candidate records by (cell - cell0, bin), bins < 2^bin_bits,
+// cells in [cell0, cell0 + cell_span); a and b ping-pong, hist holds 256 ceil(n / 4096)
+// counts; returns the buffer with the sorted records.
+CandRecord *launch_cand_sort(CandRecord *a, CandRecord *b, uint32_t *hist, int64_t n, uint32_t cell0,
+                             uint64_t cell_span, int bin_bits, cudaStream_t s, int64_t *launches);
 
 // The two FFT passes of the search for cells [c0, c0 + nc) of band `band_idx`
 // (cells of this band: c = sky * n_spin + spin, skies relative to sky base s0).

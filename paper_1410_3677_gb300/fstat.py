@@ -75,6 +75,8 @@ assert CAND_DTYPE.itemsize == C.sizeof(fstat_candidate)
 _plan_p = C.c_void_p
 _lib.fstat_plan_create.argtypes = [P(_plan_p), P(fstat_plan_desc)]
 _lib.fstat_plan_create.restype = i32
+_lib.fstat_plan_set_band.argtypes = [_plan_p, i32, P(fstat_band)]
+_lib.fstat_plan_set_band.restype = i32
 _lib.fstat_search.argtypes = [_plan_p, i64, i64]
 _lib.fstat_search.restype = i32
 _lib.fstat_candidates_get.argtypes = [_plan_p, P(fstat_candidate), i64, P(i64), P(i64)]
@@ -99,7 +101,7 @@ _lib.fstat_status_string.restype = C.c_char_p
 _lib.fstat_plan_error.argtypes = [_plan_p]
 _lib.fstat_plan_error.restype = C.c_char_p
 
-EXPORTED = ["fstat_plan_create", "fstat_search", "fstat_candidates_get", "fstat_debug_sky",
+EXPORTED = ["fstat_plan_create", "fstat_plan_set_band", "fstat_search", "fstat_candidates_get", "fstat_debug_sky",
             "fstat_plan_get_info", "fstat_plan_set_timing", "fstat_plan_kernel_stats",
             "fstat_plan_autotune",
             "fstat_cell_F_noalloc", "fstat_plan_destroy", "fstat_status_string",
@@ -124,6 +126,31 @@ def _dev_ptr(t, ctype):
     return C.cast(C.c_void_p(t.data_ptr()), P(ctype))
 
 
+def _fill_band(fb, b, on_device: bool) -> list:
+    """Marshal one band (n, dt, f_off, phi0, eps, n_fft, x or float32 x, r) into
+    an fstat_band; returns the arrays that must outlive the call."""
+    fb.n = int(b.n)
+    fb.dt, fb.f_off, fb.phi0 = float(b.dt), float(b.f_off), float(b.phi0)
+    fb.eps = float(getattr(b, "eps", 0.0))
+    fb.n_fft = int(getattr(b, "n_fft", 0) or 0)
+    if on_device:
+        if str(b.x.dtype) == "torch.float32":
+            fb.x32 = _dev_ptr(b.x, C.c_float)
+        else:
+            fb.x = _dev_ptr(b.x, f64)
+        fb.r = _dev_ptr(b.r, f64)
+        return [b.x, b.r]
+    x = np.ascontiguousarray(b.x)
+    r = np.ascontiguousarray(np.asarray(b.r, dtype=np.float64).reshape(-1))
+    if x.dtype == np.float32:
+        fb.x32 = _ptr(x, C.c_float)
+    else:
+        x = x.astype(np.float64, copy=False)
+        fb.x = _ptr(x, f64)
+    fb.r = _ptr(r, f64)
+    return [x, r]
+
+
 class Plan:
     """One search plan: fstat_plan_create / fstat_search / fstat_candidates_get.
 
@@ -137,31 +164,11 @@ class Plan:
                  stream: Optional[int] = None, on_device: bool = False, full: bool = False,
                  interbin: bool = False):
         self._keep = []
+        self._on_device = on_device
         nb = len(bands)
         arr = (fstat_band * nb)()
         for i, b in enumerate(bands):
-            fb = arr[i]
-            fb.n = int(b.n)
-            fb.dt, fb.f_off, fb.phi0 = float(b.dt), float(b.f_off), float(b.phi0)
-            fb.eps = float(getattr(b, "eps", 0.0))
-            fb.n_fft = int(getattr(b, "n_fft", 0) or 0)
-            if on_device:
-                if str(b.x.dtype) == "torch.float32":
-                    fb.x32 = _dev_ptr(b.x, C.c_float)
-                else:
-                    fb.x = _dev_ptr(b.x, f64)
-                fb.r = _dev_ptr(b.r, f64)
-                self._keep += [b.x, b.r]
-            else:
-                x = np.ascontiguousarray(b.x)
-                r = np.ascontiguousarray(np.asarray(b.r, dtype=np.float64).reshape(-1))
-                if x.dtype == np.float32:
-                    fb.x32 = _ptr(x, C.c_float)
-                else:
-                    x = x.astype(np.float64, copy=False)
-                    fb.x = _ptr(x, f64)
-                fb.r = _ptr(r, f64)
-                self._keep += [x, r]
+            self._keep += _fill_band(arr[i], b, on_device)
         if on_device:
             pa, pd, pf = (_dev_ptr(alpha, f64), _dev_ptr(delta, f64), _dev_ptr(fdot, f64))
             n_sky, n_spin = int(alpha.numel()), int(fdot.numel())
@@ -196,6 +203,15 @@ class Plan:
     def _raise(self, rc, what):
         raise FstatError(rc, f"{what}: {_lib.fstat_plan_error(self._h).decode()}")
 
+    def set_band(self, band: int, data) -> None:
+        """fstat_plan_set_band: the next segment of band `band` (same n, dt, n_fft)."""
+        fb = fstat_band()
+        keep = _fill_band(fb, data, self._on_device)
+        rc = _lib.fstat_plan_set_band(self._h, int(band), C.byref(fb))
+        del keep
+        if rc != FSTAT_OK:
+            self._raise(rc, "fstat_plan_set_band")
+
     def search(self, cell_begin: int = 0, cell_end: int = -1, allow_overflow: bool = False) -> int:
         rc = _lib.fstat_search(self._h, cell_begin, cell_end)
         if rc not in (FSTAT_OK, FSTAT_ERR_OVERFLOW) or (rc == FSTAT_ERR_OVERFLOW and not allow_overflow):
@@ -205,18 +221,28 @@ class Plan:
     def search_status(self, cell_begin: int = 0, cell_end: int = -1) -> int:
         return _lib.fstat_search(self._h, cell_begin, cell_end)
 
-    def candidates(self, cap: Optional[int] = None):
-        """(structured array sorted by (band, sky, spin, bin), n_total)."""
+    def candidates(self, cap: Optional[int] = None, out: Optional[np.ndarray] = None):
+        """(structured array sorted by (band, sky, spin, bin), n_total).  With `out`
+        (a CAND_DTYPE array, reused across calls) the records land there and a view
+        of its first n_written entries is returned; it must hold every candidate
+        unless cap limits the count."""
         nw, nt = i64(), i64()
         if cap is None:
             _lib.fstat_candidates_get(self._h, None, 0, C.byref(nw), C.byref(nt))
             cap = int(nt.value)
-        out = np.empty(max(cap, 1), CAND_DTYPE)
-        rc = _lib.fstat_candidates_get(self._h, out.ctypes.data_as(P(fstat_candidate)), cap,
+        if out is not None:
+            if out.dtype != CAND_DTYPE or not out.flags.c_contiguous or out.size < cap:
+                raise ValueError("out must be a contiguous CAND_DTYPE array of at least cap records")
+            buf = out
+        else:
+            buf = np.empty(max(cap, 1), CAND_DTYPE)
+        rc = _lib.fstat_candidates_get(self._h, buf.ctypes.data_as(P(fstat_candidate)), cap,
                                        C.byref(nw), C.byref(nt))
         if rc not in (FSTAT_OK, FSTAT_ERR_OVERFLOW):
             self._raise(rc, "fstat_candidates_get")
-        return (out if nw.value == out.size else out[:nw.value].copy()), int(nt.value)
+        if out is not None:
+            return buf[:nw.value], int(nt.value)
+        return (buf if nw.value == buf.size else buf[:nw.value].copy()), int(nt.value)
 
     def candidates_get_status(self, cap: int):
         nw, nt = i64(), i64()

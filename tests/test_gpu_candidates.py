@@ -1,0 +1,72 @@
+"""Read-back order of large candidate sets: above 65536 records the plan sorts
+them on the device (stable radix sort by cell and bin) before the copy.  With a
+threshold below every F the candidates are all searched bins of all cells, so
+the expected list is known exactly; F must equal, record for record, the F of
+the same search at a threshold whose few candidates take the host sort."""
+import numpy as np
+import pytest
+
+from paper_1410_3677_gb300 import synth as S
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def fs():
+    from paper_1410_3677_gb300 import fstat
+    return fstat
+
+
+def _plan(fs, w, thr, **kw):
+    return fs.Plan(w.bands, w.alpha, w.delta, w.fdot, thr, lat=w.lat, gamma=w.gamma,
+                   upsample=w.upsample, cand_capacity=1 << 21, **kw)
+
+
+@pytest.mark.parametrize("kw", [dict(form=1), dict(form=1, interbin=True), dict(form=0)],
+                         ids=["fp32", "fp32-interbin", "fp64"])
+def test_every_bin_in_order(fs, kw):
+    w = S.workload(1)
+    n_fft = w.bands[0].n_fft
+    p = _plan(fs, w, -1.0, **kw)
+    assert p.search() == 0, p.error()
+    c, total = p.candidates()
+    q = _plan(fs, w, 20.0, **kw)
+    assert q.search() == 0
+    few, _ = q.candidates()
+    q.close()
+    bins = np.arange(1, n_fft // 2)
+    assert total == c.size == w.n_sky * w.n_spin * bins.size > (1 << 16)
+    assert np.array_equal(c["bin"], np.tile(bins, w.n_sky * w.n_spin))
+    cell = c["sky"] * w.n_spin + c["spin"]
+    assert np.array_equal(cell, np.repeat(np.arange(w.n_sky * w.n_spin), bins.size))
+    assert np.all(c["band"] == 0)
+    # F attached to the right record: the few candidates of the higher threshold
+    idx = (few["sky"] * w.n_spin + few["spin"]) * bins.size + (few["bin"] - 1)
+    assert few.size > 0 and np.array_equal(c["F"][idx], few["F"])
+    # a second read-back of the same search gives the same list
+    c2, _ = p.candidates()
+    p.close()
+    assert np.array_equal(c, c2)
+
+
+def test_sub_range_and_multi_band_order(fs):
+    """Four float32 bands of the banded workload, a cell range that starts inside
+    band 1: the sort key is relative to the first searched cell."""
+    w = S.workload(4, n_sky=4, n_spin=2, n_bands=4)
+    p = fs.Plan(w.bands, w.alpha, w.delta, w.fdot, -1.0, lat=w.lat, gamma=w.gamma,
+                upsample=w.upsample, form=fs.FP32_BATCHED, cand_capacity=1 << 24)
+    per_band = w.n_sky * w.n_spin
+    lo, hi = per_band + 3, 3 * per_band + 5
+    assert p.search(lo, hi) == 0, p.error()
+    c, total = p.candidates()
+    p.close()
+    assert total == c.size > (1 << 16)
+    key = np.stack([c["band"], c["sky"], c["spin"], c["bin"]])
+    order = np.lexsort(key[::-1])
+    assert np.array_equal(order, np.arange(c.size))
+    cell = c["band"].astype(np.int64) * per_band + c["sky"] * w.n_spin + c["spin"]
+    assert cell.min() == lo and cell.max() == hi - 1
+    counts = np.bincount(cell - lo)
+    for k, n in enumerate(counts):
+        b = (lo + k) // per_band
+        assert n == w.bands[b].n_fft // 2 - 1
