@@ -100,8 +100,11 @@ struct InterTw {
     }
     template <int R, int JPF>
     __device__ __forceinline__ void apply(int l2, int j, float *re, float *im) const {
-        float2 w = wn(l2 * j);
-        const float2 st = wn(l2 * JPF);
+        apply<R>(wn(l2 * j), wn(l2 * JPF), re, im);
+    }
+    // the same with the two factors W^{l2 j}, W^{l2 JPF} fetched beforehand
+    template <int R>
+    __device__ __forceinline__ void apply(float2 w, const float2 st, float *re, float *im) const {
 #pragma unroll
         for (int r = 0; r < R; ++r) {
             const float xr = re[r], xi = im[r];
@@ -230,6 +233,9 @@ struct ScratchLoadTMA {
     }
     template <int R, int JPF>
     __device__ __forceinline__ void load(const eng2::Job &q, float *re, float *im) const {
+        // the twiddle factors load while the bulk copies are in flight
+        const int l2 = l2_0 + q.f;
+        const float2 w0 = tw.wn(l2 * q.j), st = tw.wn(l2 * JPF);
         if (!ptx::mbar_try_wait(bar, 0)) {
             const uint64_t t0 = ptx::globaltimer_ns();
             bool late = false;
@@ -245,7 +251,7 @@ struct ScratchLoadTMA {
             const float2 v = row[r * JPF];
             re[r] = v.x; im[r] = v.y;
         }
-        tw.template apply<R, JPF>(l2_0 + q.f, q.j, re, im);
+        tw.template apply<R>(w0, st, re, im);
     }
 };
 
@@ -435,6 +441,8 @@ struct ScratchLoadIBTMA {
     }
     template <int R, int JPF>
     __device__ __forceinline__ void load(const eng2::Job &q, float *re, float *im) const {
+        const int l2 = (l2_0 + q.f) & (C::N2 - 1);
+        const float2 w0 = tw.wn(l2 * q.j), st = tw.wn(l2 * JPF);
         if (!ptx::mbar_try_wait(bar, 0)) {
             const uint64_t t0 = ptx::globaltimer_ns();
             bool late = false;
@@ -450,7 +458,7 @@ struct ScratchLoadIBTMA {
             const float2 v = row[r * JPF];
             re[r] = v.x; im[r] = v.y;
         }
-        tw.template apply<R, JPF>((l2_0 + q.f) & (C::N2 - 1), q.j, re, im);
+        tw.template apply<R>(w0, st, re, im);
     }
 };
 
