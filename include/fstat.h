@@ -268,6 +268,20 @@ fstat_status fstat_cell_F_noalloc(const float *w, int64_t n, int64_t n_fft, doub
                                   double norm_a, double norm_b, int64_t bin_lo, int64_t bin_hi,
                                   float *F_out, void *cuda_stream);
 
+/* Roofline denominators measured on the current device (not part of the
+   method; the search path is bounded by its FFT FLOP on the CUDA cores and by
+   its inter-pass scratch bytes).  fstat_measure_fp32_fma: the FP32 rate of
+   independent FFMA chains in every lane (8 CTAs of 256 threads per SM), in
+   TFLOP/s at 2 FLOP per FMA.  fstat_measure_l2_copy: the read + write bandwidth,
+   in GB/s, of a copy of bytes/2 to another bytes/2 repeated through L2 only
+   (ld/st.global.cg), so that a working set smaller than L2 is served from it.
+   Each runs once untimed and once timed with CUDA events on cuda_stream (NULL:
+   the legacy default stream), a few milliseconds; device memory is allocated
+   and freed inside.  Errors: FSTAT_ERR_ARG (NULL output, bytes < 1 MiB),
+   FSTAT_ERR_OOM, FSTAT_ERR_CUDA. */
+fstat_status fstat_measure_fp32_fma(double *tflops, void *cuda_stream);
+fstat_status fstat_measure_l2_copy(int64_t bytes, double *gbs, void *cuda_stream);
+
 /* Release everything the plan holds.  NULL is accepted. */
 void fstat_plan_destroy(fstat_plan *plan);
 

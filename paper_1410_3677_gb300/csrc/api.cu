@@ -960,7 +960,7 @@ fstat_status fstat_candidates_get(fstat_plan *p, fstat_candidate *buf, int64_t c
                 const int64_t want = std::min<int64_t>(p->cand_capacity, kept + kept / 4);
                 const int64_t nblk = (want + 4095) / 4096;
                 if (cudaMalloc((void **)&p->cand_tmp, want * sizeof(CandRecord)) != cudaSuccess ||
-                    cudaMalloc((void **)&p->sort_hist, 256 * nblk * sizeof(uint32_t)) != cudaSuccess) {
+                    cudaMalloc((void **)&p->sort_hist, 256 * (nblk + 1) * sizeof(uint32_t)) != cudaSuccess) {
                     cudaGetLastError();
                     if (p->cand_tmp) cudaFree(p->cand_tmp);
                     p->cand_tmp = nullptr;

@@ -5,8 +5,10 @@
 // digit-major order (the tile's first slot for each digit), and a scatter that
 // ranks each record among the equal digits before it in its tile (warp match,
 // per-warp counts in shared memory), so records with equal digits keep their
-// order and the passes compose.  The candidate set of Sect. 2 has no order of
-// its own; the plan returns it sorted by (band, sky, spin, bin).
+// order and the passes compose.  The scan runs per digit row (one CTA each) and
+// the scatter adds the totals of the smaller digits.  The candidate set of
+// Sect. 2 has no order of its own; the plan returns it sorted by (band, sky,
+// spin, bin).
 #include "fstat_internal.h"
 
 namespace fstat {
@@ -38,41 +40,71 @@ __global__ void __launch_bounds__(kThreads) k_digit_hist(const CandRecord *__res
     hist[(int64_t)threadIdx.x * nblk + blockIdx.x] = h[threadIdx.x];
 }
 
-// Exclusive scan of len counts in place by one CTA: each thread sums a
-// contiguous segment, the segment sums are scanned in shared memory, and each
-// thread rewrites its segment as running offsets.
-__global__ void __launch_bounds__(1024) k_scan_counts(uint32_t *__restrict__ h, int64_t len) {
-    __shared__ uint32_t part[1024];
-    const int t = threadIdx.x;
-    const int64_t per = (len + 1023) / 1024;
-    const int64_t a = min(len, (int64_t)t * per), b = min(len, a + per);
-    uint32_t s = 0;
-    for (int64_t i = a; i < b; ++i) s += h[i];
-    part[t] = s;
+// Exclusive scan of each digit's row of tile counts in place, one CTA of 1024
+// threads per digit (coalesced chunks of 1024 counts, warp-shuffle scans); the
+// row total goes to tot[digit].
+__global__ void __launch_bounds__(1024) k_scan_rows(uint32_t *__restrict__ h, int64_t nblk,
+                                                    uint32_t *__restrict__ tot) {
+    __shared__ uint32_t wsum[32];
+    __shared__ uint32_t carry;
+    const int t = threadIdx.x, w = t >> 5, l = t & 31;
+    uint32_t *row = h + (int64_t)blockIdx.x * nblk;
+    if (t == 0) carry = 0;
     __syncthreads();
-    for (int off = 1; off < 1024; off <<= 1) {
-        const uint32_t v = t >= off ? part[t - off] : 0u;
+    for (int64_t c0 = 0; c0 < nblk; c0 += 1024) {
+        const int64_t i = c0 + t;
+        const uint32_t v = i < nblk ? row[i] : 0u;
+        uint32_t x = v;   // inclusive scan within the warp
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, x, d);
+            if (l >= d) x += y;
+        }
+        if (l == 31) wsum[w] = x;
         __syncthreads();
-        part[t] += v;
+        if (w == 0) {
+            uint32_t z = wsum[l];
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, z, d);
+                if (l >= d) z += y;
+            }
+            wsum[l] = z;   // inclusive over warps
+        }
+        __syncthreads();
+        const uint32_t before = carry + (w > 0 ? wsum[w - 1] : 0u) + x - v;
+        if (i < nblk) row[i] = before;
+        __syncthreads();
+        if (t == 0) carry += wsum[31];
         __syncthreads();
     }
-    uint32_t run = part[t] - s;
-    for (int64_t i = a; i < b; ++i) {
-        const uint32_t v = h[i];
-        h[i] = run;
-        run += v;
-    }
+    if (t == 0) tot[blockIdx.x] = carry;
 }
 
 __global__ void __launch_bounds__(kThreads) k_digit_scatter(const CandRecord *__restrict__ in,
                                                             CandRecord *__restrict__ out, int64_t n,
                                                             uint32_t cell0, int bin_bits, int shift,
-                                                            const uint32_t *__restrict__ off, int64_t nblk) {
+                                                            const uint32_t *__restrict__ off, int64_t nblk,
+                                                            const uint32_t *__restrict__ tot) {
     __shared__ uint32_t run[256];             // slots of each digit used by earlier rounds
     __shared__ uint32_t wc[kThreads / 32][256];   // this round's count of each digit per warp
+    __shared__ uint32_t wt[kThreads / 32];
     const int t = threadIdx.x, w = t >> 5, l = t & 31;
     const unsigned below = (1u << l) - 1u;
-    run[t] = off[(int64_t)t * nblk + blockIdx.x];
+    // first slot of digit t: the records of all smaller digits (an exclusive scan
+    // of the 256 row totals) plus this tile's offset within the row of digit t
+    const uint32_t v = tot[t];
+    uint32_t x = v;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, d);
+        if (l >= d) x += y;
+    }
+    if (l == 31) wt[w] = x;
+    __syncthreads();
+    uint32_t smaller = x - v;
+    for (int q = 0; q < w; ++q) smaller += wt[q];
+    run[t] = smaller + off[(int64_t)t * nblk + blockIdx.x];
     const int64_t base = (int64_t)blockIdx.x * kTile;
     for (int i = 0; i < kRounds; ++i) {
 #pragma unroll
@@ -112,7 +144,8 @@ int sort_bits(uint64_t v) {
 }
 
 // Sorts n records of `a` (using b as the other buffer of the ping-pong and hist
-// for 256 ceil(n / 4096) counts); returns the buffer that holds the result.
+// for 256 ceil(n / 4096) counts plus 256 totals); returns the buffer that holds
+// the result.
 // cell0 and the cell span are those of the searched range, bins < 2^bin_bits.
 CandRecord *launch_cand_sort(CandRecord *a, CandRecord *b, uint32_t *hist, int64_t n, uint32_t cell0,
                              uint64_t cell_span, int bin_bits, cudaStream_t s, int64_t *launches) {
@@ -123,8 +156,9 @@ CandRecord *launch_cand_sort(CandRecord *a, CandRecord *b, uint32_t *hist, int64
     for (int p = 0; p < passes; ++p) {
         const int shift = 8 * p;
         k_digit_hist<<<(unsigned)nblk, kThreads, 0, s>>>(src, n, cell0, bin_bits, shift, hist, nblk);
-        k_scan_counts<<<1, 1024, 0, s>>>(hist, 256 * nblk);
-        k_digit_scatter<<<(unsigned)nblk, kThreads, 0, s>>>(src, dst, n, cell0, bin_bits, shift, hist, nblk);
+        k_scan_rows<<<256, 1024, 0, s>>>(hist, nblk, hist + 256 * nblk);
+        k_digit_scatter<<<(unsigned)nblk, kThreads, 0, s>>>(src, dst, n, cell0, bin_bits, shift, hist, nblk,
+                                                             hist + 256 * nblk);
         *launches += 3;
         CandRecord *x = src;
         src = dst;

@@ -230,7 +230,7 @@ int launch_geometry(const Plan &p, const BandDev &b, int64_t s0, int64_t ns, boo
 // Per-sky S sums and normalisations for the ns skies of the last geometry launch.
 int launch_reduce_norms(const Plan &p, const BandDev &b, int64_t ns, double *norm, cudaStream_t s);
 // Stable device sort of n candidate records by (cell - cell0, bin), bins < 2^bin_bits,
-// cells in [cell0, cell0 + cell_span); a and b ping-pong, hist holds 256 ceil(n / 4096)
+// cells in [cell0, cell0 + cell_span); a and b ping-pong, hist holds 256 (ceil(n / 4096) + 1)
 // counts; returns the buffer with the sorted records.
 CandRecord *launch_cand_sort(CandRecord *a, CandRecord *b, uint32_t *hist, int64_t n, uint32_t cell0,
                              uint64_t cell_span, int bin_bits, cudaStream_t s, int64_t *launches);

@@ -94,6 +94,10 @@ _lib.fstat_plan_autotune.restype = i32
 _lib.fstat_cell_F_noalloc.argtypes = [C.c_void_p, i64, i64, f64, f64, f64, i64, i64,
                                        C.c_void_p, C.c_void_p]
 _lib.fstat_cell_F_noalloc.restype = i32
+_lib.fstat_measure_fp32_fma.argtypes = [P(f64), C.c_void_p]
+_lib.fstat_measure_fp32_fma.restype = i32
+_lib.fstat_measure_l2_copy.argtypes = [i64, P(f64), C.c_void_p]
+_lib.fstat_measure_l2_copy.restype = i32
 _lib.fstat_plan_destroy.argtypes = [_plan_p]
 _lib.fstat_plan_destroy.restype = None
 _lib.fstat_status_string.argtypes = [i32]
@@ -104,8 +108,27 @@ _lib.fstat_plan_error.restype = C.c_char_p
 EXPORTED = ["fstat_plan_create", "fstat_plan_set_band", "fstat_search", "fstat_candidates_get", "fstat_debug_sky",
             "fstat_plan_get_info", "fstat_plan_set_timing", "fstat_plan_kernel_stats",
             "fstat_plan_autotune",
-            "fstat_cell_F_noalloc", "fstat_plan_destroy", "fstat_status_string",
+            "fstat_cell_F_noalloc", "fstat_measure_fp32_fma", "fstat_measure_l2_copy",
+            "fstat_plan_destroy", "fstat_status_string",
             "fstat_plan_error"]
+
+
+def measure_fp32_fma(stream: Optional[int] = None) -> float:
+    """fstat_measure_fp32_fma: FP32 FMA throughput of the device, TFLOP/s."""
+    v = f64()
+    rc = _lib.fstat_measure_fp32_fma(C.byref(v), C.c_void_p(stream) if stream else None)
+    if rc != FSTAT_OK:
+        raise FstatError(rc, "fstat_measure_fp32_fma")
+    return v.value
+
+
+def measure_l2_copy(nbytes: int = 32 << 20, stream: Optional[int] = None) -> float:
+    """fstat_measure_l2_copy: read + write GB/s of an L2-resident copy of nbytes."""
+    v = f64()
+    rc = _lib.fstat_measure_l2_copy(int(nbytes), C.byref(v), C.c_void_p(stream) if stream else None)
+    if rc != FSTAT_OK:
+        raise FstatError(rc, "fstat_measure_l2_copy")
+    return v.value
 
 
 def status_string(code: int) -> str:

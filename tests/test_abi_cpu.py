@@ -119,6 +119,12 @@ def test_null_handles(fs):
     assert not h.value
     fs._lib.fstat_plan_destroy(None)
     assert fs._lib.fstat_plan_error(None) == b""
+    assert fs._lib.fstat_plan_set_band(None, 0, None) == fs.FSTAT_ERR_ARG
+    # measurement helpers check their arguments before touching a device
+    assert fs._lib.fstat_measure_fp32_fma(None, None) == fs.FSTAT_ERR_ARG
+    v = C.c_double(1.0)
+    assert fs._lib.fstat_measure_l2_copy(1000, C.byref(v), None) == fs.FSTAT_ERR_ARG
+    assert fs._lib.fstat_measure_l2_copy(1 << 24, None, None) == fs.FSTAT_ERR_ARG
 
 
 def test_both_or_neither_series_rejected(fs):

@@ -70,3 +70,15 @@ def test_sub_range_and_multi_band_order(fs):
     for k, n in enumerate(counts):
         b = (lo + k) // per_band
         assert n == w.bands[b].n_fft // 2 - 1
+
+
+def test_measured_roofline_denominators(fs):
+    """The FP32 FMA rate lies between half and 1.05x of 128 FMA lanes per SM at the
+    maximum clock; the L2-resident copy beats the HBM copy rate."""
+    import torch
+    props = torch.cuda.get_device_properties(0)
+    tf = fs.measure_fp32_fma()
+    nominal = props.multi_processor_count * 128 * 2 * 2.07e9 / 1e12
+    assert 0.5 * nominal < tf < 1.05 * nominal, (tf, nominal)
+    l2 = fs.measure_l2_copy(32 << 20)
+    assert l2 > 7000.0, l2
