@@ -13,6 +13,7 @@
 #include <string>
 #include <vector>
 
+#include "fft_engine2.cuh"
 #include "fstat_internal.h"
 
 struct fstat_plan : public fstat::Plan {};
@@ -167,13 +168,28 @@ void host_twiddles(int logn, std::vector<double> &in1, std::vector<double> &in2,
     for (int64_t k = 0; k < N2; ++k) w(k * N1, N, &hi[2 * k]);
 }
 
+// Stage-1 twiddles of the second engine's row pass: W_M^{r j}, [r][j], for the
+// row length M = N1 split as R0 R1 by the engine's plan.
+void stage1_twiddles(int logn, std::vector<double> &o) {
+    const int64_t M = int64_t(1) << log_n1(logn);
+    const int64_t R0 = eng2::radix0((int)M), R1 = eng2::radix1((int)M);
+    o.assign((size_t)(2 * R0 * R1), 0.0);
+    for (int64_t r = 0; r < R1; ++r)
+        for (int64_t j = 0; j < R0; ++j) {
+            const double a = -kTwoPi * (double)((r * j) % M) / (double)M;
+            o[(size_t)(2 * (r * R0 + j))] = cos(a);
+            o[(size_t)(2 * (r * R0 + j) + 1)] = sin(a);
+        }
+}
+
 void build_twiddles(Plan &p, const std::vector<int> &logs, int &n_alloc) {
     std::vector<double> hd;
     std::vector<size_t> offs;
     for (int lg : logs) {
-        std::vector<double> a, b, c, d;
+        std::vector<double> a, b, c, d, e;
         host_twiddles(lg, a, b, c, d);
-        for (auto *v : {&a, &b, &c, &d}) {
+        stage1_twiddles(lg, e);
+        for (auto *v : {&a, &b, &c, &d, &e}) {
             offs.push_back(hd.size());
             hd.insert(hd.end(), v->begin(), v->end());
         }
@@ -186,10 +202,11 @@ void build_twiddles(Plan &p, const std::vector<int> &logs, int &n_alloc) {
     for (size_t i = 0; i < logs.size(); ++i) {
         TwiddleSet t;
         t.logn = logs[i];
-        t.in1_d = dd + offs[4 * i]; t.in2_d = dd + offs[4 * i + 1];
-        t.lo_d = dd + offs[4 * i + 2]; t.hi_d = dd + offs[4 * i + 3];
-        t.in1_f = df + offs[4 * i]; t.in2_f = df + offs[4 * i + 1];
-        t.lo_f = df + offs[4 * i + 2]; t.hi_f = df + offs[4 * i + 3];
+        t.in1_d = dd + offs[5 * i]; t.in2_d = dd + offs[5 * i + 1];
+        t.lo_d = dd + offs[5 * i + 2]; t.hi_d = dd + offs[5 * i + 3];
+        t.in1_f = df + offs[5 * i]; t.in2_f = df + offs[5 * i + 1];
+        t.lo_f = df + offs[5 * i + 2]; t.hi_f = df + offs[5 * i + 3];
+        t.s1_f = df + offs[5 * i + 4];
         p.tw.push_back(t);
     }
 }

@@ -211,7 +211,12 @@ struct LoaderStaged<LD, decltype(void(LD::kStaged))> { static constexpr bool val
 // ZH: the stage-0 inputs r >= R0/2 (sequence elements >= M/2) are known to be
 // zero (the zero padding of a transform at least twice the series): the loader
 // is asked for R0/2 elements and the first DFT skips its zero half.
-template <typename T, int M, int SEQ, int EH, int DIR, int MAPM, class LD, class ST, bool ZH = false>
+// TWFULL: tw is the full stage-1 table W_M^{r j} laid out [r][j] (r < R1, j < R0)
+// and the twiddles are read from it through L1 (one 8-byte load per element, a
+// half-warp reading 16 consecutive j); else tw is the table W_M^m, m < M, from
+// which the power-of-two rows are staged in shared memory.
+template <typename T, int M, int SEQ, int EH, int DIR, int MAPM, class LD, class ST, bool ZH = false,
+          bool TWFULL = false>
 __device__ __forceinline__ void run_pass(LD &ld, ST &st, const T *__restrict__ tw) {
     using V = typename Vec2T<T>::type;
     constexpr int R0 = radix0(M), R1 = radix1(M);
@@ -224,8 +229,10 @@ __device__ __forceinline__ void run_pass(LD &ld, ST &st, const T *__restrict__ t
     unsigned char *smem_raw = dyn_smem();
     V *sd = reinterpret_cast<V *>(smem_raw);
     V *tws = reinterpret_cast<V *>(smem_raw + exch_bytes<T, M, SEQ>());
-    fill_twiddles<T, M, THREADS>(tws, tw);
-    if constexpr (R1 > 1) __syncthreads();
+    if constexpr (!TWFULL) {
+        fill_twiddles<T, M, THREADS>(tws, tw);
+        if constexpr (R1 > 1) __syncthreads();
+    }
 
     T re[EH], im[EH];
     constexpr int RL0 = ZH ? R0 / 2 : R0;   // stage-0 inputs that can be non-zero
@@ -267,20 +274,30 @@ __device__ __forceinline__ void run_pass(LD &ld, ST &st, const T *__restrict__ t
             // W_M^{r j}: powers of two from the table, the rest as products
             // W^{r j} = W^{h j} W^{(r - h) j}, h the top bit of r (<= LR1 - 1 products deep)
             T wr[R1], wi[R1];
+            if constexpr (TWFULL) {
+                const V *row = reinterpret_cast<const V *>(tw) + q.j;
 #pragma unroll
-            for (int b = 0; b < LR1; ++b) {
-                const V w = tws[b * R0 + q.j];
-                wr[1 << b] = w.x;
-                wi[1 << b] = DIR < 0 ? w.y : -w.y;
-            }
+                for (int r = 1; r < R1; ++r) {
+                    const V w = __ldg(row + r * R0);
+                    wr[r] = w.x;
+                    wi[r] = DIR < 0 ? w.y : -w.y;
+                }
+            } else {
 #pragma unroll
-            for (int r = 3; r < R1; ++r) {
-                int h = r;   // top bit of r (folds to a constant once unrolled)
-                h |= h >> 1; h |= h >> 2; h |= h >> 4;
-                h = (h + 1) >> 1;
-                if (h != r) {
-                    wr[r] = wr[h] * wr[r - h] - wi[h] * wi[r - h];
-                    wi[r] = wr[h] * wi[r - h] + wi[h] * wr[r - h];
+                for (int b = 0; b < LR1; ++b) {
+                    const V w = tws[b * R0 + q.j];
+                    wr[1 << b] = w.x;
+                    wi[1 << b] = DIR < 0 ? w.y : -w.y;
+                }
+#pragma unroll
+                for (int r = 3; r < R1; ++r) {
+                    int h = r;   // top bit of r (folds to a constant once unrolled)
+                    h |= h >> 1; h |= h >> 2; h |= h >> 4;
+                    h = (h + 1) >> 1;
+                    if (h != r) {
+                        wr[r] = wr[h] * wr[r - h] - wi[h] * wi[r - h];
+                        wi[r] = wr[h] * wi[r - h] + wi[h] * wr[r - h];
+                    }
                 }
             }
 #pragma unroll

@@ -349,7 +349,7 @@ __global__ void __launch_bounds__(TS, 768 / TS) k_pass2(LD ld, ST st, const floa
     ld.init(blockIdx.x, blockIdx.y, blockIdx.y);
     st.init(blockIdx.x, blockIdx.y, blockIdx.y);
     if constexpr (eng2::LoaderStaged<LD>::value) ld.stage();
-    eng2::run_pass<float, C::M, C::SEQ, C::EH, -1, MAPM, LD, ST, PASS == 1 && ZH1>(ld, st, tw);
+    eng2::run_pass<float, C::M, C::SEQ, C::EH, -1, MAPM, LD, ST, PASS == 1 && ZH1, PASS == 2>(ld, st, tw);
 }
 
 // ------------------------------------------------------------------ interbinning
@@ -493,7 +493,9 @@ k_pass2_ib(LD ld, SearchEpi2<Cfg2<LOGN, 2, TS>, false> ep, const float *__restri
     ep.init(0, blockIdx.y, blockIdx.y);
     if constexpr (eng2::LoaderStaged<LD>::value) ld.stage();
     StoreRowsSmem<C> st;
-    eng2::run_pass<float, C::M, C::SEQ, C::EH, -1, eng2::kMapW, LD, StoreRowsSmem<C>, false>(ld, st, tw);
+    // stage-1 twiddles from the shared power-of-two rows: the full table through
+    // L1 costs this kernel registers (spills) and time
+    eng2::run_pass<float, C::M, C::SEQ, C::EH, -1, eng2::kMapW, LD, StoreRowsSmem<C>, false, false>(ld, st, tw);
     __syncthreads();
     const float2 *X = reinterpret_cast<const float2 *>(eng2::dyn_smem());
     constexpr int RL = eng2::row_ld(C::M);
@@ -598,7 +600,7 @@ template <int LOGN, bool LOWER>
 __global__ void __launch_bounds__(256, 3)
 k_search_fused(SearchLoad2<Cfg2<LOGN, 1>> ld1, ScratchStore2<Cfg2<LOGN, 1>> st1,
                ScratchLoad2<Cfg2<LOGN, 2>> ld2, SearchEpi2<Cfg2<LOGN, 2>, LOWER> st2,
-               const float *__restrict__ tw_in1, const float *__restrict__ tw_in2, FusedCtl ctl) {
+               const float *__restrict__ tw_s1, const float *__restrict__ tw_in2, FusedCtl ctl) {
     using C1 = Cfg2<LOGN, 1>;
     using C2 = Cfg2<LOGN, 2>;
     constexpr int T1 = C1::TILES, T2 = C2::TILES;
@@ -647,7 +649,7 @@ k_search_fused(SearchLoad2<Cfg2<LOGN, 1>> ld1, ScratchStore2<Cfg2<LOGN, 1>> st1,
                     ld2.init((r - I1) * tpi + u, cell, slot);
                     st2.init((r - I1) * tpi + u, cell, slot);
                     eng2::run_pass<float, C2::M, C2::SEQ, C2::EH, -1, eng2::kMapW, ScratchLoad2<C2>,
-                                   SearchEpi2<C2, LOWER>, false>(ld2, st2, tw_in1);
+                                   SearchEpi2<C2, LOWER>, false, true>(ld2, st2, tw_s1);
                 }
             }
             __syncthreads();

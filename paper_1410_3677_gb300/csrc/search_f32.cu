@@ -36,7 +36,7 @@ void launch_pass2(const Plan &p, int band_idx, const BandDev &b, int64_t s0, int
     auto k2 = k_pass2<LOGN, 2, eng2::kMapW, LD2, SearchEpi2<C2, LOWER>, TS>;
     static bool attr2 = false;
     if (!attr2) { set_smem(k2, C2::SMEM + extra); attr2 = true; }
-    k2<<<dim3(C2::TILES, (unsigned)nc), C2::THREADS, C2::SMEM + extra, s>>>(ld2, st2, tw->in1_f);
+    k2<<<dim3(C2::TILES, (unsigned)nc), C2::THREADS, C2::SMEM + extra, s>>>(ld2, st2, tw->s1_f);
 }
 
 template <int LOGN, bool LOWER>
@@ -98,7 +98,7 @@ int launch_fused(const Plan &p, int band_idx, const BandDev &b, int64_t s0, int6
     }
     const int64_t items = (nc + p.fused_ahead) * (int64_t)(C1::TILES / tpi + C2::TILES / tpi);
     const unsigned grid = (unsigned)std::min<int64_t>(items, resident);
-    k<<<grid, 256, smem, s>>>(ld1, st1, ld2, st2, tw->in1_f, tw->in2_f, ctl);
+    k<<<grid, 256, smem, s>>>(ld1, st1, ld2, st2, tw->s1_f, tw->in2_f, ctl);
     return 1;
 }
 
