@@ -101,20 +101,84 @@ __device__ __forceinline__ void dft(T *re, T *im) {
     else eng::dft<R, DIR>(re, im);
 }
 
-// R-point DFT of x[0 .. R/2) with x[R/2 .. R) = 0: the even outputs are the
-// R/2-point DFT of x, the odd ones that of x_r W_R^r (the first radix-2 layer
-// of a decimation in frequency, whose partners are all zero).
-template <int R, int DIR, typename T>
+// 4-point DFT whose inputs from index NZ on are known to be zero: the terms
+// with a zero partner are left out (the compiler may not drop x + 0 itself,
+// since -0 + 0 = +0 under IEEE rules).
+template <int DIR, int NZ, typename T>
+__device__ __forceinline__ void dft4z(T &r0, T &i0, T &r1, T &i1, T &r2, T &i2, T &r3, T &i3) {
+    static_assert(NZ >= 1 && NZ <= 4, "non-zero inputs");
+    if constexpr (NZ == 4) {
+        eng::dft4<DIR>(r0, i0, r1, i1, r2, i2, r3, i3);
+    } else {
+        // t0 = x0 + x2, t1 = x0 - x2, t2 = t3 = x1 (x3 = 0); u = (DIR i) x1
+        const T t0r = NZ >= 3 ? r0 + r2 : r0, t0i = NZ >= 3 ? i0 + i2 : i0;
+        const T t1r = NZ >= 3 ? r0 - r2 : r0, t1i = NZ >= 3 ? i0 - i2 : i0;
+        if constexpr (NZ == 1) {
+            r1 = r2 = r3 = r0;
+            i1 = i2 = i3 = i0;
+        } else {
+            const T ur = DIR < 0 ? i1 : -i1, ui = DIR < 0 ? -r1 : r1;
+            const T x1r = r1, x1i = i1;
+            r0 = t0r + x1r; i0 = t0i + x1i;
+            r2 = t0r - x1r; i2 = t0i - x1i;
+            r1 = t1r + ur;  i1 = t1i + ui;
+            r3 = t1r - ur;  i3 = t1i - ui;
+        }
+    }
+}
+
+// 16-point DFT (radix-4 decimation in time, as dft_r4) of x[0 .. NZ) with
+// x[NZ .. 16) = 0: the sub-DFT over x[4m + q] keeps its ceil((NZ - q)/4)
+// non-zero inputs; the elements from NZ on are not read.
+template <int DIR, int NZ, typename T>
+__device__ __forceinline__ void dft16z(T *re, T *im) {
+    static_assert(NZ >= 4 && NZ <= 16, "each sub-DFT keeps an input");
+    T sr[4][4], si[4][4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+        for (int m = 0; m < 4; ++m)
+            if (4 * m + q < NZ) { sr[q][m] = re[4 * m + q]; si[q][m] = im[4 * m + q]; }
+            else { sr[q][m] = T(0); si[q][m] = T(0); }   // never read below
+    dft4z<DIR, (NZ + 3) / 4>(sr[0][0], si[0][0], sr[0][1], si[0][1], sr[0][2], si[0][2], sr[0][3], si[0][3]);
+    dft4z<DIR, (NZ + 2) / 4>(sr[1][0], si[1][0], sr[1][1], si[1][1], sr[1][2], si[1][2], sr[1][3], si[1][3]);
+    dft4z<DIR, (NZ + 1) / 4>(sr[2][0], si[2][0], sr[2][1], si[2][1], sr[2][2], si[2][2], sr[2][3], si[2][3]);
+    dft4z<DIR, NZ / 4>(sr[3][0], si[3][0], sr[3][1], si[3][1], sr[3][2], si[3][2], sr[3][3], si[3][3]);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        T zr[4], zi[4];
+        zr[0] = sr[0][k]; zi[0] = si[0][k];
+#pragma unroll
+        for (int q = 1; q < 4; ++q) {
+            zr[q] = sr[q][k];
+            zi[q] = si[q][k];
+            mul_w32<DIR>(2 * q * k, zr[q], zi[q]);   // W_16^{q k} = W_32^{2 q k}
+        }
+        eng::dft4<DIR>(zr[0], zi[0], zr[1], zi[1], zr[2], zi[2], zr[3], zi[3]);
+#pragma unroll
+        for (int p = 0; p < 4; ++p) { re[k + 4 * p] = zr[p]; im[k + 4 * p] = zi[p]; }
+    }
+}
+
+// R-point DFT of x[0 .. NZ) with x[NZ .. R) = 0, NZ <= R/2: the even outputs are
+// the R/2-point DFT of x, the odd ones that of x_r W_R^r (the first radix-2
+// layer of a decimation in frequency, whose partners are all zero); below R/2
+// non-zero inputs the half-length DFTs skip their zero inputs too (R = 32).
+template <int R, int DIR, int NZ = R / 2, typename T>
 __device__ __forceinline__ void dft_half_zero(T *re, T *im) {
     constexpr int H = R / 2;
+    static_assert(NZ <= H && (NZ == H || H == 16), "pruned half-length DFTs are 16-point");
     T er[H], ei[H], orr[H], oi[H];
 #pragma unroll
-    for (int r = 0; r < H; ++r) {
+    for (int r = 0; r < NZ; ++r) {
         er[r] = re[r]; ei[r] = im[r];
         orr[r] = re[r]; oi[r] = im[r];
         mul_w32<DIR>((32 / R) * r, orr[r], oi[r]);
     }
-    if constexpr (H > 1) {
+    if constexpr (NZ < H) {
+        dft16z<DIR, NZ>(er, ei);
+        dft16z<DIR, NZ>(orr, oi);
+    } else if constexpr (H > 1) {
         dft<H, DIR>(er, ei);
         dft<H, DIR>(orr, oi);
     }
@@ -208,14 +272,16 @@ struct LoaderStaged { static constexpr bool value = false; };
 template <class LD>
 struct LoaderStaged<LD, decltype(void(LD::kStaged))> { static constexpr bool value = LD::kStaged; };
 
-// ZH: the stage-0 inputs r >= R0/2 (sequence elements >= M/2) are known to be
-// zero (the zero padding of a transform at least twice the series): the loader
-// is asked for R0/2 elements and the first DFT skips its zero half.
+// ZQ: the stage-0 inputs r >= R0 ZQ/8 (sequence elements >= M ZQ/8) are known
+// to be zero (the zero padding of a transform at least 8/ZQ times the series):
+// the loader is asked for R0 ZQ/8 elements and the first DFT skips the zeros
+// (ZQ = 8: none known; 4: the upper half known zero; 3: the upper five eighths
+// known zero, R0 = 32 only).
 // TWFULL: tw is the full stage-1 table W_M^{r j} laid out [r][j] (r < R1, j < R0)
 // and the twiddles are read from it through L1 (one 8-byte load per element, a
 // half-warp reading 16 consecutive j); else tw is the table W_M^m, m < M, from
 // which the power-of-two rows are staged in shared memory.
-template <typename T, int M, int SEQ, int EH, int DIR, int MAPM, class LD, class ST, bool ZH = false,
+template <typename T, int M, int SEQ, int EH, int DIR, int MAPM, class LD, class ST, int ZQ = 8,
           bool TWFULL = false>
 __device__ __forceinline__ void run_pass(LD &ld, ST &st, const T *__restrict__ tw) {
     using V = typename Vec2T<T>::type;
@@ -235,12 +301,13 @@ __device__ __forceinline__ void run_pass(LD &ld, ST &st, const T *__restrict__ t
     }
 
     T re[EH], im[EH];
-    constexpr int RL0 = ZH ? R0 / 2 : R0;   // stage-0 inputs that can be non-zero
+    static_assert(ZQ == 8 || ZQ == 4 || (ZQ == 3 && R0 == 32), "known-zero fraction of the first stage");
+    constexpr int RL0 = R0 * ZQ / 8;   // stage-0 inputs that can be non-zero
 #pragma unroll
     for (int i = 0; i < NJ0; ++i) ld.template load<RL0, JPF0>(job<MAPM, SEQ, TPF, THREADS>(i), &re[i * R0], &im[i * R0]);
 #pragma unroll
     for (int i = 0; i < NJ0; ++i) {
-        if constexpr (ZH) dft_half_zero<R0, DIR>(&re[i * R0], &im[i * R0]);
+        if constexpr (ZQ < 8) dft_half_zero<R0, DIR, RL0>(&re[i * R0], &im[i * R0]);
         else dft<R0, DIR>(&re[i * R0], &im[i * R0]);
     }
     if constexpr (R1 == 1) {

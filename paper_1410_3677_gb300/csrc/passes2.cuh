@@ -338,18 +338,20 @@ struct SearchEpi2 {
 
 // Three CTAs per SM: <= 85 registers (pass 1 loads half its column, pass 2
 // keeps no demodulation or twiddle-power state) and 3 x 68 KB of shared memory.
-// Pass 1 of a search transform (N_fft >= 2n) reads only the first half of each
-// column: elements k2 >= N2/2 lie at k >= N/2 >= n, in the zero padding.
-// ZH1 = false: pass 1 of a transform only as long as the series allows (the
-// half-length transform of the interbinning form, N >= n but not N >= 2n).
-template <int LOGN, int PASS, int MAPM, class LD, class ST, int TS = 256, bool ZH1 = true>
+// Z1: eighths of each pass-1 column that can be non-zero.  Pass 1 of a search
+// transform (N_fft >= 2n) reads only the first half of each column (Z1 = 4):
+// elements k2 >= N2/2 lie at k >= N/2 >= n, in the zero padding; with
+// n <= 3N/8 and a radix-32 first stage only the first three eighths (Z1 = 3);
+// Z1 = 8: a transform only as long as the series allows (the half-length
+// transform of the interbinning form, N >= n but not N >= 2n).
+template <int LOGN, int PASS, int MAPM, class LD, class ST, int TS = 256, int Z1 = 4>
 __global__ void __launch_bounds__(TS, 768 / TS) k_pass2(LD ld, ST st, const float *__restrict__ tw) {
     using C = Cfg2<LOGN, PASS, TS>;
     if constexpr (PASS == 2) ld.prefetch_ahead();
     ld.init(blockIdx.x, blockIdx.y, blockIdx.y);
     st.init(blockIdx.x, blockIdx.y, blockIdx.y);
     if constexpr (eng2::LoaderStaged<LD>::value) ld.stage();
-    eng2::run_pass<float, C::M, C::SEQ, C::EH, -1, MAPM, LD, ST, PASS == 1 && ZH1, PASS == 2>(ld, st, tw);
+    eng2::run_pass<float, C::M, C::SEQ, C::EH, -1, MAPM, LD, ST, PASS == 1 ? Z1 : 8, PASS == 2>(ld, st, tw);
 }
 
 // ------------------------------------------------------------------ interbinning
@@ -495,7 +497,7 @@ k_pass2_ib(LD ld, SearchEpi2<Cfg2<LOGN, 2, TS>, false> ep, const float *__restri
     StoreRowsSmem<C> st;
     // stage-1 twiddles from the shared power-of-two rows: the full table through
     // L1 costs this kernel registers (spills) and time
-    eng2::run_pass<float, C::M, C::SEQ, C::EH, -1, eng2::kMapW, LD, StoreRowsSmem<C>, false, false>(ld, st, tw);
+    eng2::run_pass<float, C::M, C::SEQ, C::EH, -1, eng2::kMapW, LD, StoreRowsSmem<C>, 8, false>(ld, st, tw);
     __syncthreads();
     const float2 *X = reinterpret_cast<const float2 *>(eng2::dyn_smem());
     constexpr int RL = eng2::row_ld(C::M);
@@ -640,7 +642,7 @@ k_search_fused(SearchLoad2<Cfg2<LOGN, 1>> ld1, ScratchStore2<Cfg2<LOGN, 1>> st1,
                     ld1.init(r * tpi + u, cell, slot);
                     st1.init(r * tpi + u, cell, slot);
                     eng2::run_pass<float, C1::M, C1::SEQ, C1::EH, -1, eng2::kMapFJ, SearchLoad2<C1>,
-                                   ScratchStore2<C1>, true>(ld1, st1, tw_in2);
+                                   ScratchStore2<C1>, 4>(ld1, st1, tw_in2);
                 }
             } else {
 #pragma unroll 1
@@ -649,7 +651,7 @@ k_search_fused(SearchLoad2<Cfg2<LOGN, 1>> ld1, ScratchStore2<Cfg2<LOGN, 1>> st1,
                     ld2.init((r - I1) * tpi + u, cell, slot);
                     st2.init((r - I1) * tpi + u, cell, slot);
                     eng2::run_pass<float, C2::M, C2::SEQ, C2::EH, -1, eng2::kMapW, ScratchLoad2<C2>,
-                                   SearchEpi2<C2, LOWER>, false, true>(ld2, st2, tw_s1);
+                                   SearchEpi2<C2, LOWER>, 8, true>(ld2, st2, tw_s1);
                 }
             }
             __syncthreads();

@@ -46,8 +46,19 @@ int launch_two(const Plan &p, int band_idx, const BandDev &b, int64_t s0, int64_
                const TwiddleSet *tw) {
     using C1 = Cfg2<LOGN, 1>;
     using C2 = Cfg2<LOGN, 2>;
-    {
-        auto k1 = k_pass2<LOGN, 1, eng2::kMapFJ, SearchLoad2<C1>, ScratchStore2<C1>>;
+    // columns known zero beyond 3/8 of their length (radix-32 first stage) or 1/2
+    bool launched = false;
+    if constexpr (eng2::radix0(C1::M) == 32) {
+        if (8 * b.n <= 3 * (int64_t)C1::N) {
+            auto k1 = k_pass2<LOGN, 1, eng2::kMapFJ, SearchLoad2<C1>, ScratchStore2<C1>, 256, 3>;
+            static bool attr3 = false;
+            if (!attr3) { set_smem(k1, C1::SMEM); attr3 = true; }
+            k1<<<dim3(C1::TILES, (unsigned)nc), C1::THREADS, C1::SMEM, s>>>(ld1, st1, tw->in2_f);
+            launched = true;
+        }
+    }
+    if (!launched) {
+        auto k1 = k_pass2<LOGN, 1, eng2::kMapFJ, SearchLoad2<C1>, ScratchStore2<C1>, 256, 4>;
         static bool attr1 = false;
         if (!attr1) { set_smem(k1, C1::SMEM); attr1 = true; }
         k1<<<dim3(C1::TILES, (unsigned)nc), C1::THREADS, C1::SMEM, s>>>(ld1, st1, tw->in2_f);
@@ -152,7 +163,7 @@ int launch_interbin(const Plan &p, int band_idx, const BandDev &b, int64_t s0, i
     ld1.s0 = s0;
     ScratchStore2<C1> st1{};
     st1.scratch = reinterpret_cast<float2 *>(cb.scratch);
-    auto k1 = k_pass2<LOGN, 1, eng2::kMapFJ, SearchLoad2<C1>, ScratchStore2<C1>, 256, false>;
+    auto k1 = k_pass2<LOGN, 1, eng2::kMapFJ, SearchLoad2<C1>, ScratchStore2<C1>, 256, 8>;
     static bool attr1 = false;
     if (!attr1) { set_smem(k1, C1::SMEM); attr1 = true; }
     k1<<<dim3(C1::TILES, (unsigned)nc), C1::THREADS, C1::SMEM, s>>>(ld1, st1, tw->in2_f);
