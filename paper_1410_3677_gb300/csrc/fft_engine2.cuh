@@ -194,15 +194,22 @@ __host__ __device__ constexpr int radix0(int M) { return M <= 32 ? M : (M >= 512
 __host__ __device__ constexpr int radix1(int M) { return M <= 32 ? 1 : M / radix0(M); }
 __host__ __device__ constexpr int pad(int i) { return i + (i >> 5); }
 __host__ __device__ constexpr int row_ld(int M) { return (pad(M - 1) + 1) | 1; }
+// 16-byte exchange layout of the column passes (two stage-1 jobs per thread):
+// two padding elements per 32 keep pairs (2i, 2i + 1) together and 16-byte
+// aligned, and a row length of 2 mod 4 elements spreads the 8 lanes of a
+// quarter-warp (consecutive sequences) over all eight 16-byte bank groups.
+__host__ __device__ constexpr bool x16_layout(int M, int EH) { return M > 32 && EH == 2 * radix1(M) && radix0(M) % 2 == 0; }
+__host__ __device__ constexpr int pad16(int i) { return i + 2 * (i >> 5); }
+__host__ __device__ constexpr int row_ld16(int M) { return (pad16(M - 1) + 1) + ((6 - (pad16(M - 1) + 1) % 4) % 4); }
 // stage-1 twiddles: rows b < log2 R1 of W_M^{2^b j}, j < R0
 __host__ __device__ constexpr int ilog2c(int x) { return x <= 1 ? 0 : 1 + ilog2c(x >> 1); }
 __host__ __device__ constexpr int tw_entries(int M) { return M <= 32 ? 1 : ilog2c(radix1(M)) * radix0(M); }
 
-template <typename T, int M, int SEQ>
-__host__ __device__ constexpr size_t exch_bytes() { return 2 * sizeof(T) * (size_t)SEQ * row_ld(M); }
-template <typename T, int M, int SEQ>
+template <typename T, int M, int SEQ, bool X16 = false>
+__host__ __device__ constexpr size_t exch_bytes() { return 2 * sizeof(T) * (size_t)SEQ * (X16 ? row_ld16(M) : row_ld(M)); }
+template <typename T, int M, int SEQ, bool X16 = false>
 __host__ __device__ constexpr size_t smem_bytes() {
-    return exch_bytes<T, M, SEQ>() + 2 * sizeof(T) * (size_t)tw_entries(M);
+    return exch_bytes<T, M, SEQ, X16>() + 2 * sizeof(T) * (size_t)tw_entries(M);
 }
 
 // Mappings of a thread's i-th job of a stage to (sequence s, butterfly j) and of
@@ -288,13 +295,28 @@ __device__ __forceinline__ void run_pass(LD &ld, ST &st, const T *__restrict__ t
     constexpr int R0 = radix0(M), R1 = radix1(M);
     constexpr int TPF = M / EH;
     constexpr int THREADS = SEQ * TPF;
-    constexpr int RL = row_ld(M);
+    // column mapping with two stage-1 jobs per thread: 16-byte exchange, the
+    // thread's stage-1 jobs being the neighbours j and j + 1
+    constexpr bool X16 = MAPM == kMapFJ && x16_layout(M, EH) && sizeof(T) == 4;
+    constexpr int RL = X16 ? row_ld16(M) : row_ld(M);
     constexpr int JPF0 = M / R0, NJ0 = EH / R0;
     static_assert(EH % R0 == 0 && (R1 == 1 || EH % R1 == 0), "elements per thread vs radix");
     static_assert(MAPM != kMapW || (TPF <= 16 && 32 % TPF == 0), "warp mapping needs <= 16 threads per sequence");
     unsigned char *smem_raw = dyn_smem();
     V *sd = reinterpret_cast<V *>(smem_raw);
-    V *tws = reinterpret_cast<V *>(smem_raw + exch_bytes<T, M, SEQ>());
+    V *tws = reinterpret_cast<V *>(smem_raw + exch_bytes<T, M, SEQ, X16>());
+    auto job1 = [](int i) -> Job {   // stage-1 job i of this thread
+        if constexpr (X16) {
+            Job q;
+            q.s = (int)threadIdx.x % SEQ;
+            q.j = 2 * ((int)threadIdx.x / SEQ) + i;
+            q.t = q.s & 1;
+            q.f = q.s >> 1;
+            return q;
+        } else {
+            return job<MAPM, SEQ, TPF, THREADS>(i);
+        }
+    };
     if constexpr (!TWFULL) {
         fill_twiddles<T, M, THREADS>(tws, tw);
         if constexpr (R1 > 1) __syncthreads();
@@ -321,22 +343,41 @@ __device__ __forceinline__ void run_pass(LD &ld, ST &st, const T *__restrict__ t
 #pragma unroll
         for (int i = 0; i < NJ0; ++i) {
             const Job q = job<MAPM, SEQ, TPF, THREADS>(i);
-            V *p = sd + q.s * RL + pad(q.j * R0);
+            if constexpr (X16) {   // outputs r, r + 1 side by side (j R0 + r stays in one 32-block)
+                float4 *p4 = reinterpret_cast<float4 *>(sd + q.s * RL + pad16(q.j * R0));
 #pragma unroll
-            for (int r = 0; r < R0; ++r) p[pad(r)] = V{re[i * R0 + r], im[i * R0 + r]};
+                for (int r = 0; r < R0; r += 2)
+                    p4[r / 2] = make_float4(re[i * R0 + r], im[i * R0 + r], re[i * R0 + r + 1], im[i * R0 + r + 1]);
+            } else {
+                V *p = sd + q.s * RL + pad(q.j * R0);
+#pragma unroll
+                for (int r = 0; r < R0; ++r) p[pad(r)] = V{re[i * R0 + r], im[i * R0 + r]};
+            }
         }
         if constexpr (MAPM == kMapW) __syncwarp(); else __syncthreads();
         constexpr int NJ1 = EH / R1;
         constexpr int LR1 = ilog2c(R1);
 #pragma unroll
         for (int i = 0; i < NJ1; ++i) {
-            const Job q = job<MAPM, SEQ, TPF, THREADS>(i);   // q.j < R0
-            const V *p = sd + q.s * RL + pad(q.j);
+            const Job q = job1(i);   // q.j < R0
             T *xr = &re[i * R1], *xi = &im[i * R1];
+            if constexpr (X16) {
+                if (i == 0) {   // one 16-byte load per r serves both jobs (j even, j + 1)
+                    const float4 *p4 = reinterpret_cast<const float4 *>(sd + q.s * RL + q.j);
 #pragma unroll
-            for (int r = 0; r < R1; ++r) {
-                const V v = p[pad(r * R0)];
-                xr[r] = v.x; xi[r] = v.y;
+                    for (int r = 0; r < R1; ++r) {
+                        const float4 v = p4[pad16(r * R0) / 2];
+                        re[r] = v.x; im[r] = v.y;
+                        re[R1 + r] = v.z; im[R1 + r] = v.w;
+                    }
+                }
+            } else {
+                const V *p = sd + q.s * RL + pad(q.j);
+#pragma unroll
+                for (int r = 0; r < R1; ++r) {
+                    const V v = p[pad(r * R0)];
+                    xr[r] = v.x; xi[r] = v.y;
+                }
             }
             // W_M^{r j}: powers of two from the table, the rest as products
             // W^{r j} = W^{h j} W^{(r - h) j}, h the top bit of r (<= LR1 - 1 products deep)
@@ -378,7 +419,7 @@ __device__ __forceinline__ void run_pass(LD &ld, ST &st, const T *__restrict__ t
         }
         if constexpr (!StoreEarly<ST>::value) {
 #pragma unroll
-            for (int i = 0; i < NJ1; ++i) st.template store<R1, R0>(job<MAPM, SEQ, TPF, THREADS>(i), &re[i * R1], &im[i * R1]);
+            for (int i = 0; i < NJ1; ++i) st.template store<R1, R0>(job1(i), &re[i * R1], &im[i * R1]);
         }
     }
 }

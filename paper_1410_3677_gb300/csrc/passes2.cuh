@@ -31,7 +31,7 @@ struct Cfg2 {
     static constexpr int F = SEQ / 2;                    // columns / rows per tile
     static constexpr int THREADS = SEQ * TPF;
     static constexpr int TILES = OTHER / F;
-    static constexpr size_t SMEM = eng2::smem_bytes<float, M, SEQ>();
+    static constexpr size_t SMEM = eng2::smem_bytes<float, M, SEQ, PASS == 1 && eng2::x16_layout(M, EH)>();
     static constexpr int MINB = 768 / TS;                // CTAs per SM (24 warps)
     static_assert(M >= 64 && THREADS == TS, "tile shape");
 };
