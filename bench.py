@@ -412,7 +412,8 @@ def run_ours(args, rank, world, dist):
             h2d += hb.x.nbytes + hb.r.nbytes
             hbs.append(hb)
         al, de, fd = pinned(w.alpha), pinned(w.delta), pinned(w.fdot)
-        n_e2e = max(1, min(args.steps, 3))
+        n_e2e = max(3, min(args.steps, 5))
+        w_e2e = 2     # the first search runs plainly, the second is captured as a CUDA graph
 
         def make_plan():
             return fstat.Plan(hbs, al, de, fd, w.thr_2F, lat=w.lat, gamma=w.gamma,
@@ -423,7 +424,7 @@ def run_ours(args, rank, world, dist):
         p = make_plan()
         times, d2h = [], 0
         out = None      # the caller's candidate array, reused across segments
-        for it in range(n_e2e + 1):
+        for it in range(n_e2e + w_e2e):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             for bi, hb in enumerate(hbs):
@@ -436,7 +437,7 @@ def run_ours(args, rank, world, dist):
                 out = np.empty(c.size + c.size // 4 + 1024, fstat.CAND_DTYPE)
                 out.view(np.uint8)[:] = 0     # resident before the timed steps
             torch.cuda.synchronize()
-            if it > 0:
+            if it >= w_e2e:
                 times.append(time.perf_counter() - t0)
             d2h = int(c.size) * 16 + 8
         p.close()
@@ -455,7 +456,7 @@ def run_ours(args, rank, world, dist):
                 times_pc.append(time.perf_counter() - t0)
         e2e = {"value": nb_total * world / statistics.mean(times), "unit": UNIT,
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
-               "steps": n_e2e,
+               "steps": n_e2e, "warmup": w_e2e,
                "with_plan_create": {"value": nb_total * world / statistics.mean(times_pc),
                                     "ms_per_step": 1e3 * statistics.mean(times_pc),
                                     "h2d_bytes_per_step": int(h2d + h2d_grid)},
