@@ -82,3 +82,31 @@ def test_set_band_rejects_another_shape(fs):
     # the plan is still usable after the refusals
     assert p.search() == 0
     p.close()
+
+
+def test_replaced_segment_from_device_memory(fs):
+    """inputs_on_device = 1: the segments are torch CUDA tensors (float32 series)."""
+    import torch
+    w = S.workload(1)
+    segs = [_segment(w, 21, np.float32), _segment(w, 22, np.float32)]
+
+    def dev(b):
+        class D:
+            pass
+        d = D()
+        d.n, d.dt, d.f_off, d.phi0, d.eps, d.n_fft = b.n, b.dt, b.f_off, b.phi0, b.eps, b.n_fft
+        d.x = torch.from_numpy(np.ascontiguousarray(b.x)).cuda()
+        d.r = torch.from_numpy(np.ascontiguousarray(b.r).reshape(-1)).cuda()
+        return d
+
+    grid = [torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in (w.alpha, w.delta, w.fdot)]
+    p = fs.Plan([dev(segs[0])], *grid, w.thr_2F, lat=w.lat, gamma=w.gamma, upsample=w.upsample,
+                form=fs.FP32_BATCHED, cand_capacity=1 << 20, on_device=True)
+    _cands(p)
+    p.set_band(0, dev(segs[1]))
+    got = _cands(p)
+    p.close()
+    q = _plan(fs, w, segs[1], fs.FP32_BATCHED)
+    want = _cands(q)
+    q.close()
+    assert got.size == want.size > 0 and np.array_equal(got, want)
