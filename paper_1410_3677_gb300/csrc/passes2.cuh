@@ -1,9 +1,12 @@
 // The two FP32 search passes on the second FFT engine (one transform per thread
 // group, 32 elements per thread, two register stages per pass).  Same four-step
 // split and scratch layout as the first engine's passes: pass 1 transforms the
-// columns k1 (length N2) of the demodulated series and writes them, twiddled by
-// W_N^{k1 l2} and transposed, to scratch; pass 2 transforms the rows l2 (length
-// N1) and evaluates F on every bin it produces.
+// columns k1 (length N2) of the demodulated series and writes them transposed to
+// scratch; pass 2 twiddles the rows l2 by W_N^{k1 l2}, transforms them (length
+// N1) and evaluates F on every bin it produces.  Scratch holds the two
+// transforms interleaved, A[l2][k1][t] (t = 0: F_a, 1: F_b), so a warp's store
+// of 8 columns of both transforms is one 128-byte run and a pass-2 tile of rows
+// is one contiguous block.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -131,11 +134,11 @@ struct ScratchStore2 {
     }
     template <int R, int JPF>
     __device__ __forceinline__ void store(const eng2::Job &q, float *re, float *im) const {
-        float2 *dst = base + (int64_t)q.t * C::N + (int64_t)q.j * C::N1 + k1_0 + q.f;
+        float2 *dst = base + 2 * ((int64_t)q.j * C::N1 + k1_0 + q.f) + q.t;
 #pragma unroll
         for (int r = 0; r < R; ++r) {
             __stcg(dst, float2{re[r], im[r]});
-            dst += JPF * C::N1;
+            dst += 2 * JPF * C::N1;
         }
     }
 };
@@ -153,8 +156,9 @@ struct ScratchLoad2 {
         l2_0 = tile * C::F;
     }
     // The rows of the tile `pf_dist` CTAs further in launch order go to L2 ahead of
-    // their CTA (two contiguous 32 KB runs, one per transform), so the DRAM reads
-    // of pass 2 run behind its computation instead of at the start of every CTA.
+    // their CTA (one contiguous run of F rows of both transforms), so the DRAM
+    // reads of pass 2 run behind its computation instead of at the start of
+    // every CTA.
     __device__ void prefetch_ahead() const {
         if (pf_dist <= 0 || threadIdx.x != 0) return;
         const int64_t b = blockIdx.x + (int64_t)gridDim.x * blockIdx.y + pf_dist;
@@ -162,28 +166,27 @@ struct ScratchLoad2 {
         if (b >= total) return;
         const int64_t slot = b / gridDim.x;
         const int tile = (int)(b - slot * gridDim.x);
-        const float2 *rows = scratch + slot * 2 * C::N + (int64_t)tile * C::F * C::N1;
-        constexpr uint32_t bytes = (uint32_t)(C::F * C::N1 * sizeof(float2));
-        ptx::bulk_prefetch_l2(rows, bytes);
-        ptx::bulk_prefetch_l2(rows + C::N, bytes);
+        const float2 *rows = scratch + slot * 2 * C::N + 2 * (int64_t)tile * C::F * C::N1;
+        ptx::bulk_prefetch_l2(rows, (uint32_t)(2 * C::F * C::N1 * sizeof(float2)));
     }
     template <int R, int JPF>
     __device__ __forceinline__ void load(const eng2::Job &q, float *re, float *im) const {
-        const float2 *row = base + (int64_t)q.t * C::N + (int64_t)(l2_0 + q.f) * C::N1 + q.j;
+        const float2 *row = base + 2 * ((int64_t)(l2_0 + q.f) * C::N1 + q.j) + q.t;
 #pragma unroll
         for (int r = 0; r < R; ++r) {
-            const float2 v = __ldcg(row + r * JPF);
+            const float2 v = __ldcg(row + 2 * r * JPF);
             re[r] = v.x; im[r] = v.y;
         }
         tw.template apply<R, JPF>(l2_0 + q.f, q.j, re, im);
     }
 };
 
-// Pass 2 input staged by the TMA unit: the tile's rows are two contiguous runs
-// of F N1 complex floats (one per transform) in scratch; one thread copies both
-// into the CTA's exchange area with bulk copies completing on an mbarrier, and
-// the threads then read their butterflies' elements from shared memory (rows
-// unpadded there: a half-warp reads 16 consecutive elements, conflict-free).
+// Pass 2 input staged by the TMA unit: the tile's rows are one contiguous run of
+// 2 F N1 complex floats in scratch (both transforms interleaved); one thread
+// copies it into the CTA's exchange area with a bulk copy completing on an
+// mbarrier, and the threads then read their butterflies' elements from shared
+// memory (a warp reads 32 consecutive elements, F_a and F_b alternating:
+// conflict-free).
 // The run_pass of a staged loader synchronises the CTA before the first scatter
 // overwrites the staged rows.
 template <class C>
@@ -195,10 +198,10 @@ struct ScratchLoadTMA {
     InterTw<C::LOGN1> tw;
     int l2_0;
     const float2 *src;
-    const float2 *rows;     // staged rows in shared memory: [t F + f][N1]
+    const float2 *rows;     // staged rows in shared memory: [f][N1][t]
     uint64_t *bar;
     __device__ void init(int tile, int64_t, int64_t slot) {
-        src = scratch + slot * 2 * C::N + (int64_t)tile * C::F * C::N1;
+        src = scratch + slot * 2 * C::N + 2 * (int64_t)tile * C::F * C::N1;
         l2_0 = tile * C::F;
         unsigned char *sm = eng2::dyn_smem();
         rows = reinterpret_cast<const float2 *>(sm);
@@ -211,24 +214,21 @@ struct ScratchLoadTMA {
         if (b >= total) return;
         const int64_t slot = b / gridDim.x;
         const int tile = (int)(b - slot * gridDim.x);
-        const float2 *r = scratch + slot * 2 * C::N + (int64_t)tile * C::F * C::N1;
-        constexpr uint32_t bytes = (uint32_t)(C::F * C::N1 * sizeof(float2));
-        ptx::bulk_prefetch_l2(r, bytes);
-        ptx::bulk_prefetch_l2(r + C::N, bytes);
+        const float2 *r = scratch + slot * 2 * C::N + 2 * (int64_t)tile * C::F * C::N1;
+        ptx::bulk_prefetch_l2(r, (uint32_t)(2 * C::F * C::N1 * sizeof(float2)));
     }
-    // issue the copies (the whole CTA calls this once, before run_pass)
+    // issue the copy (the whole CTA calls this once, before run_pass)
     __device__ void stage() const {
-        constexpr uint32_t bytes = (uint32_t)(C::F * C::N1 * sizeof(float2));
-        static_assert(2 * bytes <= eng2::exch_bytes<float, C::M, C::SEQ>(), "staged rows fit the exchange area");
+        constexpr uint32_t bytes = (uint32_t)(2 * C::F * C::N1 * sizeof(float2));
+        static_assert(bytes <= eng2::exch_bytes<float, C::M, C::SEQ>(), "staged rows fit the exchange area");
         if (threadIdx.x == 0) {
             ptx::mbar_init(bar, 1);
             ptx::fence_mbar_init();
         }
         __syncthreads();
         if (threadIdx.x == 0) {
-            ptx::mbar_arrive_expect_tx(bar, 2 * bytes);
+            ptx::mbar_arrive_expect_tx(bar, bytes);
             ptx::bulk_g2s(const_cast<float2 *>(rows), src, bytes, bar);
-            ptx::bulk_g2s(const_cast<float2 *>(rows) + C::F * C::N1, src + C::N, bytes, bar);
         }
     }
     template <int R, int JPF>
@@ -245,10 +245,10 @@ struct ScratchLoadTMA {
                 if (dt > 2000000000ull) break;   // reported above; results are discarded
             }
         }
-        const float2 *row = rows + (q.t * C::F + q.f) * C::N1 + q.j;
+        const float2 *row = rows + 2 * (q.f * C::N1 + q.j) + q.t;
 #pragma unroll
         for (int r = 0; r < R; ++r) {
-            const float2 v = row[r * JPF];
+            const float2 v = row[2 * r * JPF];
             re[r] = v.x; im[r] = v.y;
         }
         tw.template apply<R>(w0, st, re, im);
@@ -377,19 +377,20 @@ struct ScratchLoadIB {
     template <int R, int JPF>
     __device__ __forceinline__ void load(const eng2::Job &q, float *re, float *im) const {
         const int l2 = (l2_0 + q.f) & (C::N2 - 1);
-        const float2 *row = base + (int64_t)q.t * C::N + (int64_t)l2 * C::N1 + q.j;
+        const float2 *row = base + 2 * ((int64_t)l2 * C::N1 + q.j) + q.t;
 #pragma unroll
         for (int r = 0; r < R; ++r) {
-            const float2 v = __ldcg(row + r * JPF);
+            const float2 v = __ldcg(row + 2 * r * JPF);
             re[r] = v.x; im[r] = v.y;
         }
         tw.template apply<R, JPF>(l2, q.j, re, im);
     }
 };
 
-// The same rows staged by the TMA unit: per transform one bulk copy of the rows
-// l2_0 .. N2 - 1 that the tile holds and, for the last tile, one of the rows it
-// wraps to from row 0; the tile F - 1 rows ahead is prefetched into L2.
+// The same rows staged by the TMA unit: one bulk copy of the rows l2_0 .. N2 - 1
+// that the tile holds (both transforms, interleaved) and, for the last tile, one
+// of the rows it wraps to from row 0; the tile F - 1 rows ahead is prefetched
+// into L2.
 template <class C>
 struct ScratchLoadIBTMA {
     static constexpr bool kStaged = true;
@@ -416,10 +417,8 @@ struct ScratchLoadIBTMA {
         const int64_t slot = b / gridDim.x;
         const int l2 = (int)(b - slot * gridDim.x) * (C::F - 1);
         const int nr = C::N2 - l2 < C::F ? C::N2 - l2 : C::F;
-        const float2 *r = scratch + slot * 2 * C::N + (int64_t)l2 * C::N1;
-        const uint32_t bytes = (uint32_t)(nr * C::N1 * sizeof(float2));
-        ptx::bulk_prefetch_l2(r, bytes);
-        ptx::bulk_prefetch_l2(r + C::N, bytes);
+        const float2 *r = scratch + slot * 2 * C::N + 2 * (int64_t)l2 * C::N1;
+        ptx::bulk_prefetch_l2(r, (uint32_t)(2 * nr * C::N1 * sizeof(float2)));
     }
     __device__ void stage() const {
         static_assert(2 * C::F * C::N1 * sizeof(float2) <= eng2::exch_bytes<float, C::M, C::SEQ>(),
@@ -431,14 +430,11 @@ struct ScratchLoadIBTMA {
         __syncthreads();
         if (threadIdx.x == 0) {
             const int na = C::N2 - l2_0 < C::F ? C::N2 - l2_0 : C::F;   // rows before the wrap
-            const uint32_t row_bytes = (uint32_t)(C::N1 * sizeof(float2));
-            ptx::mbar_arrive_expect_tx(bar, 2 * C::F * row_bytes);
-            for (int t = 0; t < 2; ++t) {
-                float2 *dst = const_cast<float2 *>(rows) + t * C::F * C::N1;
-                const float2 *plane = base + (int64_t)t * C::N;
-                ptx::bulk_g2s(dst, plane + (int64_t)l2_0 * C::N1, na * row_bytes, bar);
-                if (na < C::F) ptx::bulk_g2s(dst + na * C::N1, plane, (C::F - na) * row_bytes, bar);
-            }
+            const uint32_t row_bytes = (uint32_t)(2 * C::N1 * sizeof(float2));   // both transforms
+            float2 *dst = const_cast<float2 *>(rows);
+            ptx::mbar_arrive_expect_tx(bar, C::F * row_bytes);
+            ptx::bulk_g2s(dst, base + 2 * (int64_t)l2_0 * C::N1, na * row_bytes, bar);
+            if (na < C::F) ptx::bulk_g2s(dst + 2 * na * C::N1, base, (C::F - na) * row_bytes, bar);
         }
     }
     template <int R, int JPF>
@@ -454,10 +450,10 @@ struct ScratchLoadIBTMA {
                 if (dt > 2000000000ull) break;   // reported above; results are discarded
             }
         }
-        const float2 *row = rows + (q.t * C::F + q.f) * C::N1 + q.j;
+        const float2 *row = rows + 2 * (q.f * C::N1 + q.j) + q.t;
 #pragma unroll
         for (int r = 0; r < R; ++r) {
-            const float2 v = row[r * JPF];
+            const float2 v = row[2 * r * JPF];
             re[r] = v.x; im[r] = v.y;
         }
         tw.template apply<R>(w0, st, re, im);
