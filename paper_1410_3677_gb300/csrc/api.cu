@@ -168,10 +168,10 @@ void host_twiddles(int logn, std::vector<double> &in1, std::vector<double> &in2,
     for (int64_t k = 0; k < N2; ++k) w(k * N1, N, &hi[2 * k]);
 }
 
-// Stage-1 twiddles of the second engine's row pass: W_M^{r j}, [r][j], for the
-// row length M = N1 split as R0 R1 by the engine's plan.
-void stage1_twiddles(int logn, std::vector<double> &o) {
-    const int64_t M = int64_t(1) << log_n1(logn);
+// Stage-1 twiddles of the second engine: W_M^{r j}, [r][j], for a pass length M
+// (N1 of the rows, N2 of the columns) split as R0 R1 by the engine's plan.
+void stage1_twiddles(int logm, std::vector<double> &o) {
+    const int64_t M = int64_t(1) << logm;
     const int64_t R0 = eng2::radix0((int)M), R1 = eng2::radix1((int)M);
     o.assign((size_t)(2 * R0 * R1), 0.0);
     for (int64_t r = 0; r < R1; ++r)
@@ -186,10 +186,11 @@ void build_twiddles(Plan &p, const std::vector<int> &logs, int &n_alloc) {
     std::vector<double> hd;
     std::vector<size_t> offs;
     for (int lg : logs) {
-        std::vector<double> a, b, c, d, e;
+        std::vector<double> a, b, c, d, e, f;
         host_twiddles(lg, a, b, c, d);
-        stage1_twiddles(lg, e);
-        for (auto *v : {&a, &b, &c, &d, &e}) {
+        stage1_twiddles(log_n1(lg), e);
+        stage1_twiddles(log_n2(lg), f);
+        for (auto *v : {&a, &b, &c, &d, &e, &f}) {
             offs.push_back(hd.size());
             hd.insert(hd.end(), v->begin(), v->end());
         }
@@ -202,11 +203,11 @@ void build_twiddles(Plan &p, const std::vector<int> &logs, int &n_alloc) {
     for (size_t i = 0; i < logs.size(); ++i) {
         TwiddleSet t;
         t.logn = logs[i];
-        t.in1_d = dd + offs[5 * i]; t.in2_d = dd + offs[5 * i + 1];
-        t.lo_d = dd + offs[5 * i + 2]; t.hi_d = dd + offs[5 * i + 3];
-        t.in1_f = df + offs[5 * i]; t.in2_f = df + offs[5 * i + 1];
-        t.lo_f = df + offs[5 * i + 2]; t.hi_f = df + offs[5 * i + 3];
-        t.s1_f = df + offs[5 * i + 4];
+        t.in1_d = dd + offs[6 * i]; t.in2_d = dd + offs[6 * i + 1];
+        t.lo_d = dd + offs[6 * i + 2]; t.hi_d = dd + offs[6 * i + 3];
+        t.in1_f = df + offs[6 * i]; t.in2_f = df + offs[6 * i + 1];
+        t.lo_f = df + offs[6 * i + 2]; t.hi_f = df + offs[6 * i + 3];
+        t.s1_f = df + offs[6 * i + 4]; t.s2_f = df + offs[6 * i + 5];
         p.tw.push_back(t);
     }
 }

@@ -31,9 +31,9 @@ struct TwiddleSet {
     // device pointers, interleaved (re, im); float and double copies
     const double *in1_d = nullptr, *in2_d = nullptr, *lo_d = nullptr, *hi_d = nullptr;
     const float *in1_f = nullptr, *in2_f = nullptr, *lo_f = nullptr, *hi_f = nullptr;
-    // second engine, pass 2 (rows of length N1 = R0 R1): stage-1 twiddles
-    // W_N1^{r j} laid out [r][j], r < R1, j < R0 (float)
-    const float *s1_f = nullptr;
+    // second engine: stage-1 twiddles W_M^{r j} laid out [r][j], r < R1, j < R0
+    // (float), for the rows (M = N1 = R0 R1, pass 2) and the columns (M = N2, pass 1)
+    const float *s1_f = nullptr, *s2_f = nullptr;
 };
 
 // Device record of one candidate: global cell index, bin and F.

@@ -351,7 +351,7 @@ __global__ void __launch_bounds__(TS, 768 / TS) k_pass2(LD ld, ST st, const floa
     ld.init(blockIdx.x, blockIdx.y, blockIdx.y);
     st.init(blockIdx.x, blockIdx.y, blockIdx.y);
     if constexpr (eng2::LoaderStaged<LD>::value) ld.stage();
-    eng2::run_pass<float, C::M, C::SEQ, C::EH, -1, MAPM, LD, ST, PASS == 1 ? Z1 : 8, PASS == 2>(ld, st, tw);
+    eng2::run_pass<float, C::M, C::SEQ, C::EH, -1, MAPM, LD, ST, PASS == 1 ? Z1 : 8, true>(ld, st, tw);
 }
 
 // ------------------------------------------------------------------ interbinning
@@ -598,7 +598,7 @@ template <int LOGN, bool LOWER>
 __global__ void __launch_bounds__(256, 3)
 k_search_fused(SearchLoad2<Cfg2<LOGN, 1>> ld1, ScratchStore2<Cfg2<LOGN, 1>> st1,
                ScratchLoad2<Cfg2<LOGN, 2>> ld2, SearchEpi2<Cfg2<LOGN, 2>, LOWER> st2,
-               const float *__restrict__ tw_s1, const float *__restrict__ tw_in2, FusedCtl ctl) {
+               const float *__restrict__ tw_s1, const float *__restrict__ tw_s2, FusedCtl ctl) {
     using C1 = Cfg2<LOGN, 1>;
     using C2 = Cfg2<LOGN, 2>;
     constexpr int T1 = C1::TILES, T2 = C2::TILES;
@@ -638,7 +638,7 @@ k_search_fused(SearchLoad2<Cfg2<LOGN, 1>> ld1, ScratchStore2<Cfg2<LOGN, 1>> st1,
                     ld1.init(r * tpi + u, cell, slot);
                     st1.init(r * tpi + u, cell, slot);
                     eng2::run_pass<float, C1::M, C1::SEQ, C1::EH, -1, eng2::kMapFJ, SearchLoad2<C1>,
-                                   ScratchStore2<C1>, 4>(ld1, st1, tw_in2);
+                                   ScratchStore2<C1>, 4, true>(ld1, st1, tw_s2);
                 }
             } else {
 #pragma unroll 1

@@ -53,7 +53,7 @@ int launch_two(const Plan &p, int band_idx, const BandDev &b, int64_t s0, int64_
             auto k1 = k_pass2<LOGN, 1, eng2::kMapFJ, SearchLoad2<C1>, ScratchStore2<C1>, 256, 3>;
             static bool attr3 = false;
             if (!attr3) { set_smem(k1, C1::SMEM); attr3 = true; }
-            k1<<<dim3(C1::TILES, (unsigned)nc), C1::THREADS, C1::SMEM, s>>>(ld1, st1, tw->in2_f);
+            k1<<<dim3(C1::TILES, (unsigned)nc), C1::THREADS, C1::SMEM, s>>>(ld1, st1, tw->s2_f);
             launched = true;
         }
     }
@@ -61,7 +61,7 @@ int launch_two(const Plan &p, int band_idx, const BandDev &b, int64_t s0, int64_
         auto k1 = k_pass2<LOGN, 1, eng2::kMapFJ, SearchLoad2<C1>, ScratchStore2<C1>, 256, 4>;
         static bool attr1 = false;
         if (!attr1) { set_smem(k1, C1::SMEM); attr1 = true; }
-        k1<<<dim3(C1::TILES, (unsigned)nc), C1::THREADS, C1::SMEM, s>>>(ld1, st1, tw->in2_f);
+        k1<<<dim3(C1::TILES, (unsigned)nc), C1::THREADS, C1::SMEM, s>>>(ld1, st1, tw->s2_f);
     }
     if (mid) record_timing_event(mid, s);
     if (p.tma && p.p2_threads == 128) {   // smaller tiles, six CTAs per SM
@@ -109,7 +109,7 @@ int launch_fused(const Plan &p, int band_idx, const BandDev &b, int64_t s0, int6
     }
     const int64_t items = (nc + p.fused_ahead) * (int64_t)(C1::TILES / tpi + C2::TILES / tpi);
     const unsigned grid = (unsigned)std::min<int64_t>(items, resident);
-    k<<<grid, 256, smem, s>>>(ld1, st1, ld2, st2, tw->s1_f, tw->in2_f, ctl);
+    k<<<grid, 256, smem, s>>>(ld1, st1, ld2, st2, tw->s1_f, tw->s2_f, ctl);
     return 1;
 }
 
@@ -166,7 +166,7 @@ int launch_interbin(const Plan &p, int band_idx, const BandDev &b, int64_t s0, i
     auto k1 = k_pass2<LOGN, 1, eng2::kMapFJ, SearchLoad2<C1>, ScratchStore2<C1>, 256, 8>;
     static bool attr1 = false;
     if (!attr1) { set_smem(k1, C1::SMEM); attr1 = true; }
-    k1<<<dim3(C1::TILES, (unsigned)nc), C1::THREADS, C1::SMEM, s>>>(ld1, st1, tw->in2_f);
+    k1<<<dim3(C1::TILES, (unsigned)nc), C1::THREADS, C1::SMEM, s>>>(ld1, st1, tw->s2_f);
     if (mid) record_timing_event(mid, s);
     if (p.tma) {   // 128-thread row tiles staged by bulk copies (8-byte mbarrier after the smem)
         using D2 = Cfg2<LOGN, 2, 128>;
