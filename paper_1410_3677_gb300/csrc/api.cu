@@ -342,7 +342,7 @@ void create_impl(Plan &p, const fstat_plan_desc *d) {
     p.dbuf = dalloc<double>(p, (size_t)p.sky_batch * p.n_max * (fp32 ? 2 : 1), n_alloc);
     p.partials = dalloc<double>(p, std::max<int64_t>((int64_t)p.sky_batch * nblk * 3, 256), n_alloc);
     p.S = dalloc<double>(p, 3 * p.sky_batch, n_alloc);
-    for (int q = 0; q < 2; ++q) p.normbuf[q] = dalloc<double>(p, 4 * p.sky_batch, n_alloc);
+    for (int q = 0; q < 2; ++q) p.normbuf[q] = dalloc<double>(p, kNormStride * p.sky_batch, n_alloc);
 
     // FFT scratch: cell slots of 2 transforms; also hosts the generic FFT of the upsample
     const size_t tsz = fp32 ? sizeof(float2) : sizeof(double2);

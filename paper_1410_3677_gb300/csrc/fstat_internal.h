@@ -36,6 +36,10 @@ struct TwiddleSet {
     const float *s1_f = nullptr, *s2_f = nullptr;
 };
 
+// Per-sky normaliser record: na, nb, nab, 0 in FP64 (doubles 0..3), then the
+// same four as floats (doubles 4..5), padded to 8 doubles.
+constexpr int kNormStride = 8;
+
 // Device record of one candidate: global cell index, bin and F.
 struct CandRecord {
     uint32_t cell;

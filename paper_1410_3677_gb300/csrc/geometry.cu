@@ -373,10 +373,16 @@ __global__ void k_reduce_norms(const double *__restrict__ partials, int nblk,
             na = out[0] > 0.0 ? 1.0 / (s2 * out[0]) : 0.0;
             nb = out[1] > 0.0 ? 1.0 / (s2 * out[1]) : 0.0;
         }
-        norm[4 * sl] = na;
-        norm[4 * sl + 1] = nb;
-        norm[4 * sl + 2] = nab;
-        norm[4 * sl + 3] = 0.0;
+        norm[kNormStride * sl] = na;
+        norm[kNormStride * sl + 1] = nb;
+        norm[kNormStride * sl + 2] = nab;
+        norm[kNormStride * sl + 3] = 0.0;
+        // FP32 copies for the FP32 epilogues (no conversion in every CTA)
+        float *nf = reinterpret_cast<float *>(norm + kNormStride * sl + 4);
+        nf[0] = (float)na;
+        nf[1] = (float)nb;
+        nf[2] = (float)nab;
+        nf[3] = 0.f;
     }
 }
 

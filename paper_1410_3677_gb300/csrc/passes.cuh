@@ -301,9 +301,9 @@ struct SearchEpi {
     __device__ void init() {
         const int64_t c = c0 + blockIdx.y;
         const int64_t sky = c / n_spin;
-        na = (T)norm[4 * (sky - s0)];
-        nb = (T)norm[4 * (sky - s0) + 1];
-        nab = (T)norm[4 * (sky - s0) + 2];
+        na = (T)norm[kNormStride * (sky - s0)];
+        nb = (T)norm[kNormStride * (sky - s0) + 1];
+        nab = (T)norm[kNormStride * (sky - s0) + 2];
         cell = cell_base + (uint32_t)c;
         l2_0 = blockIdx.x * C::F;
     }

@@ -264,7 +264,8 @@ struct ScratchLoadTMA {
 // l1 < N1/2 (r < R/2) are used and the rest of the last DFT is never computed.
 template <class C, bool LOWER>
 struct SearchEpi2 {
-    const double *norm;      // [sky_local][4]: na, nb, nab (F = na|F_a|^2 + nb|F_b|^2 + nab Re F_a F_b*)
+    const double *norm;      // per local sky (stride kNormStride): na, nb, nab (F = na|F_a|^2 + nb|F_b|^2
+                             // + nab Re F_a F_b*) in FP64, then the same as floats
     int n_spin;
     int64_t c0, s0;
     uint32_t cell_base;      // first global cell index of this band
@@ -279,9 +280,10 @@ struct SearchEpi2 {
     __device__ void init(int tile, int64_t cl, int64_t) {
         const int64_t c = c0 + cl;
         const int64_t sky = c / n_spin;
-        na = (float)norm[4 * (sky - s0)];
-        nb = (float)norm[4 * (sky - s0) + 1];
-        nab = (float)norm[4 * (sky - s0) + 2];
+        const float *nf = reinterpret_cast<const float *>(norm + kNormStride * (sky - s0) + 4);
+        na = nf[0];
+        nb = nf[1];
+        nab = nf[2];
         cell = cell_base + (uint32_t)c;
         l2_0 = tile * C::F;
         thr_half = 0.5f * thr;   // 2F > thr  <=>  F > thr / 2, both sides exact

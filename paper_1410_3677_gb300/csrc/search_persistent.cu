@@ -308,9 +308,9 @@ __global__ void __launch_bounds__(kThreads, 3) k_search_persistent(PArgs a) {
                 StageLoadP2<C> ld;
                 ld.stg = reinterpret_cast<const float2 *>(bp);
                 SearchEpi<float, C> st;
-                st.na = (float)a.norm[4 * (sky - a.s0)];
-                st.nb = (float)a.norm[4 * (sky - a.s0) + 1];
-                st.nab = (float)a.norm[4 * (sky - a.s0) + 2];
+                st.na = (float)a.norm[kNormStride * (sky - a.s0)];
+                st.nb = (float)a.norm[kNormStride * (sky - a.s0) + 1];
+                st.nab = (float)a.norm[kNormStride * (sky - a.s0) + 2];
                 st.cell = a.cell_base + (uint32_t)cell;
                 st.l2_0 = tic * P::F2;
                 st.bin_lo = a.bin_lo;
