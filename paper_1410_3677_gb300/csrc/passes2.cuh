@@ -56,7 +56,7 @@ struct SearchLoad2 {
     // tile: column block; cell: cell of the launch; slot: scratch slot
     __device__ void init(int tile, int64_t cell, int64_t) {
         const int64_t c = c0 + cell;
-        const int64_t sky = c / n_spin;
+        const int64_t sky = (int64_t)((uint32_t)c / (uint32_t)n_spin);   // cells < 2^32: 32-bit divide
         ws = reinterpret_cast<const float2 *>(w + (sky - s0) * w_stride);
         afx = chirp[c - sky * n_spin];
         k1_0 = tile * C::F;
@@ -164,8 +164,8 @@ struct ScratchLoad2 {
         const int64_t b = blockIdx.x + (int64_t)gridDim.x * blockIdx.y + pf_dist;
         const int64_t total = (int64_t)gridDim.x * gridDim.y;
         if (b >= total) return;
-        const int64_t slot = b / gridDim.x;
-        const int tile = (int)(b - slot * gridDim.x);
+        const int64_t slot = (uint32_t)b / gridDim.x;   // b < 2^32
+        const int tile = (int)((uint32_t)b - (uint32_t)slot * gridDim.x);
         const float2 *rows = scratch + slot * 2 * C::N + 2 * (int64_t)tile * C::F * C::N1;
         ptx::bulk_prefetch_l2(rows, (uint32_t)(2 * C::F * C::N1 * sizeof(float2)));
     }
@@ -212,8 +212,8 @@ struct ScratchLoadTMA {
         const int64_t b = blockIdx.x + (int64_t)gridDim.x * blockIdx.y + pf_dist;
         const int64_t total = (int64_t)gridDim.x * gridDim.y;
         if (b >= total) return;
-        const int64_t slot = b / gridDim.x;
-        const int tile = (int)(b - slot * gridDim.x);
+        const int64_t slot = (uint32_t)b / gridDim.x;   // b < 2^32
+        const int tile = (int)((uint32_t)b - (uint32_t)slot * gridDim.x);
         const float2 *r = scratch + slot * 2 * C::N + 2 * (int64_t)tile * C::F * C::N1;
         ptx::bulk_prefetch_l2(r, (uint32_t)(2 * C::F * C::N1 * sizeof(float2)));
     }
@@ -279,7 +279,7 @@ struct SearchEpi2 {
     int l2_0;
     __device__ void init(int tile, int64_t cl, int64_t) {
         const int64_t c = c0 + cl;
-        const int64_t sky = c / n_spin;
+        const int64_t sky = (int64_t)((uint32_t)c / (uint32_t)n_spin);   // cells < 2^32: 32-bit divide
         const float *nf = reinterpret_cast<const float *>(norm + kNormStride * (sky - s0) + 4);
         na = nf[0];
         nb = nf[1];
@@ -416,8 +416,8 @@ struct ScratchLoadIBTMA {
         const int64_t b = blockIdx.x + (int64_t)gridDim.x * blockIdx.y + pf_dist;
         const int64_t total = (int64_t)gridDim.x * gridDim.y;
         if (b >= total) return;
-        const int64_t slot = b / gridDim.x;
-        const int l2 = (int)(b - slot * gridDim.x) * (C::F - 1);
+        const int64_t slot = (uint32_t)b / gridDim.x;   // b < 2^32
+        const int l2 = (int)((uint32_t)b - (uint32_t)slot * gridDim.x) * (C::F - 1);
         const int nr = C::N2 - l2 < C::F ? C::N2 - l2 : C::F;
         const float2 *r = scratch + slot * 2 * C::N + 2 * (int64_t)l2 * C::N1;
         ptx::bulk_prefetch_l2(r, (uint32_t)(2 * nr * C::N1 * sizeof(float2)));
