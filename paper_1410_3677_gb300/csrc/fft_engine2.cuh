@@ -9,7 +9,9 @@
 // by W_M^{r j} and takes radix-R1 DFTs; outputs land at j + r R0.  Shared memory
 // holds complex elements (float2) in rows of LD elements with element i at
 // i + i/32, which makes both scatter and gather of the two-stage plan free of
-// bank conflicts for M = 512 and leaves every radix offset an immediate.
+// bank conflicts for M = 512 and leaves every radix offset an immediate; the
+// column passes with two stage-1 jobs per thread use i + 2 (i/32) instead and
+// exchange pairs of elements in 16-byte accesses (x16_layout below).
 #pragma once
 
 #include <cuda_runtime.h>

@@ -338,8 +338,8 @@ struct SearchEpi2 {
     }
 };
 
-// Three CTAs per SM: <= 85 registers (pass 1 loads half its column, pass 2
-// keeps no demodulation or twiddle-power state) and 3 x 68 KB of shared memory.
+// Pass 1: three CTAs of 256 threads per SM (<= 85 registers, about 70 KB of
+// shared memory each); pass 2: six CTAs of 128 threads.
 // Z1: eighths of each pass-1 column that can be non-zero.  Pass 1 of a search
 // transform (N_fft >= 2n) reads only the first half of each column (Z1 = 4):
 // elements k2 >= N2/2 lie at k >= N/2 >= n, in the zero padding; with
