@@ -13,6 +13,7 @@
 #include <string>
 #include <vector>
 
+#include "dfloat.cuh"
 #include "fft_engine2.cuh"
 #include "fstat_internal.h"
 
@@ -94,6 +95,12 @@ SkyConst sky_const(double al, double de, double lat, double gamma) {
     c.ny = cd * sin(al);
     c.nz = sd;
     c.alpha = al;
+    const double nv[3] = {c.nx, c.ny, c.nz};
+    for (int i = 0; i < 3; ++i) {
+        const DF d = df_from_double(nv[i]);
+        c.nf[2 * i] = d.hi;
+        c.nf[2 * i + 1] = d.lo;
+    }
     c.A[0] = (1.0 / 16.0) * s2g * (3.0 - c2l) * (3.0 - c2d);   // cos 2h
     c.A[1] = -0.25 * c2g * sl * (3.0 - c2d);                   // sin 2h
     c.A[2] = 0.25 * s2g * s2l * s2d;                           // cos h
@@ -278,6 +285,7 @@ void create_impl(Plan &p, const fstat_plan_desc *d) {
         p.n_max = std::max(p.n_max, b.n);
         b.x = dalloc<double>(p, b.n, n_alloc);
         b.r = dalloc<double>(p, 3 * b.n, n_alloc);
+        if (fp32) b.r2 = dalloc<DF>(p, 3 * b.n, n_alloc);
         b.sigma2 = dalloc<double>(p, 1, n_alloc);
         b.xu = fp32 ? (void *)dalloc<float>(p, (size_t)U * b.n, n_alloc)
                     : (void *)dalloc<double>(p, (size_t)U * b.n, n_alloc);
@@ -524,6 +532,7 @@ void band_prologue(Plan &p, BandDev &b) {
     if (t) { e0 = ev_get(p); e1 = ev_get(p); rec_timing(e0, p.stream); }
     p.launches += launch_sigma2(b.x, b.n, p.desc.sigma2, p.partials, b.sigma2, p.stream);
     p.launches += launch_upsample(p, b, p.desc.upsample, b.xu, fp32, p.stream);
+    if (fp32) p.launches += launch_split_r(b, p.stream);
     if (t) { rec_timing(e1, p.stream); p.pending.push_back({idx, e0, e1}); }
 }
 

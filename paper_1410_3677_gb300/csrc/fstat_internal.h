@@ -54,6 +54,7 @@ struct SkyConst {
     double nx, ny, nz, alpha;
     double A[5];
     double B[4];
+    float nf[6];   // nx, ny, nz as double-float pairs (hi, lo) for the FP32 delay
 };
 
 // Band data resident on the device.
@@ -66,6 +67,7 @@ struct BandDev {
     double *x = nullptr;      // [n] float64 (converted from float32 when needed)
     float *x32 = nullptr;     // [n] staging of a float32 series (allocated on first use)
     double *r = nullptr;      // [3n]
+    void *r2 = nullptr;       // FP32 form: r as double-float pairs (DF[3n]), redone per search
     double *sigma2 = nullptr; // device scalar
     void *xu = nullptr;       // [U n]: double (FP64 form) or float (FP32 form)
 };
@@ -209,6 +211,8 @@ struct CellBufs {
 
 // sigma^2 = (1/n) sum x^2, compensated, into *out (device); user_sigma2 > 0 overrides.
 // partials: >= 256 doubles.
+// FP32 form, per band and search: the ephemeris as double-float pairs (b.r2).
+int launch_split_r(const BandDev &b, cudaStream_t s);
 int launch_sigma2(const double *x, int64_t n, double user_sigma2, double *partials, double *out,
                   cudaStream_t s);
 

@@ -8,6 +8,7 @@
 //             FP64 compensated sums S_aa, S_bb, S_ab.
 #include <math.h>
 
+#include "dfloat.cuh"
 #include "fstat_internal.h"
 
 namespace fstat {
@@ -88,7 +89,8 @@ __global__ void k_sigma2_final(const double *__restrict__ partials, int nblk, in
 }
 
 // ------------------------------------------------------------------ geometry
-// FP32 form: the delay of sample j reduced once, in FP64, to the sample shift
+// FP32 form: the delay of sample j reduced once, in double-float arithmetic
+// (FP64 runs at 1/64 of the FP32 rate on GB300), to the sample shift
 // d_j / dt = I + phi (integer part exact, fraction in FP32) and to the
 // band-offset phase f_off d_j mod 1 with its increment f_off (d_{j+1} - d_j), so
 // that the detector-time inversion and the phase interpolation run in integer
@@ -147,35 +149,53 @@ __global__ void __launch_bounds__(256) k_delays(const double *__restrict__ r,
     if (k < n) d[(int64_t)sl * stride + k] = delay_at(r, sky[s0 + sl], k);
 }
 
-// Shift records of every sample of skies [s0, s0 + gridDim.y); d_{k+1} comes
-// from the next lane (the last lane of a warp evaluates it).  The increment of
-// the last sample is never used (the interpolation segment index is <= n - 2).
-__global__ void __launch_bounds__(256) k_delays_split(const double *__restrict__ r,
+// The ephemeris of a band as double-float pairs (once per search of the band).
+__global__ void k_split_r(const double *__restrict__ r, int64_t m, DF *__restrict__ r2) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < m) r2[i] = df_from_double(r[i]);
+}
+
+// Shift records of every sample of skies [s0, s0 + gridDim.y): the delay
+// nhat . r_k and its reductions in double-float arithmetic (about 2^-46
+// relative: 1e-11 samples and 1e-9 cycles at the delays and offsets of a
+// search, against the 6e-8 of the FP32 results); d_{k+1} of the phase
+// increment comes from the next thread (the block's first thread evaluates
+// the one past the block).  The increment of the last sample is never used
+// (the interpolation segment index is <= n - 2).
+__global__ void __launch_bounds__(256) k_delays_split(const DF *__restrict__ r2,
                                                       const SkyConst *__restrict__ sky, int64_t s0,
-                                                      int64_t n, int64_t stride, double inv_dt,
-                                                      double f_off, DelayRec *__restrict__ out) {
+                                                      int64_t n, int64_t stride, DF inv_dt, DF f_off,
+                                                      int phase, DelayRec *__restrict__ out) {
     const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const int sl = blockIdx.y;
-    __shared__ double dsh[257];
-    const SkyConst sc = sky[s0 + sl];
-    const double dk = k < n ? delay_at(r, sc, k) : 0.0;
+    __shared__ DF dsh[257];
+    const float *nf = sky[s0 + sl].nf;
+    const DF nx{nf[0], nf[1]}, ny{nf[2], nf[3]}, nz{nf[4], nf[5]};
+    auto delay = [&](int64_t j) {
+        const DF *rj = r2 + 3 * j;
+        return df_add(df_add(df_mul(nx, rj[0]), df_mul(ny, rj[1])), df_mul(nz, rj[2]));
+    };
+    const DF dk = k < n ? delay(k) : DF{0.f, 0.f};
     DelayRec o;
-    const double sh = dk * inv_dt;
-    const double fl = floor(sh);
-    o.I = (int)fl;
-    o.phi = (float)(sh - fl);
+    float phi;
+    o.I = (int)df_split_floor(df_mul(dk, inv_dt), &phi);
+    o.phi = phi;
     o.psi = 0.f;
     o.dpsi = 0.f;
-    if (f_off != 0.0) {   // uniform: no phase records for a band at zero offset
+    if (phase) {   // uniform: no phase records for a band at zero offset
         dsh[threadIdx.x] = dk;
         if (threadIdx.x == 0) {
             const int64_t kn = k + blockDim.x;
-            dsh[blockDim.x] = kn < n ? delay_at(r, sc, kn) : 0.0;
+            dsh[blockDim.x] = kn < n ? delay(kn) : DF{0.f, 0.f};
         }
         __syncthreads();
-        const double cyc = f_off * dk;
-        o.psi = (float)(cyc - floor(cyc));
-        if (k + 1 < n) o.dpsi = (float)(f_off * (dsh[threadIdx.x + 1] - dk));
+        float psi;
+        df_split_floor(df_mul(f_off, dk), &psi);
+        o.psi = psi;
+        if (k + 1 < n) {
+            const DF dd = df_add(dsh[threadIdx.x + 1], df_neg(dk));
+            o.dpsi = (f_off.hi + f_off.lo) * (dd.hi + dd.lo);
+        }
     }
     if (k < n) out[(int64_t)sl * stride + k] = o;
 }
@@ -469,6 +489,12 @@ inline unsigned blocks(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 }  // namespace
 
 // ================================================================== launchers
+int launch_split_r(const BandDev &b, cudaStream_t s) {
+    const int64_t m = 3 * b.n;
+    k_split_r<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(b.r, m, static_cast<DF *>(b.r2));
+    return 1;
+}
+
 int launch_sigma2(const double *x, int64_t n, double user_sigma2, double *partials,
                   double *out, cudaStream_t s) {
     constexpr int nblk = 256;
@@ -566,8 +592,9 @@ int launch_geometry(const Plan &p, const BandDev &b, int64_t s0, int64_t ns, boo
     g.dbg_mask = dbg_mask;
     dim3 grid(g.nblk, (unsigned)ns);
     if (fp32) {
-        k_delays_split<<<grid, 256, 0, s>>>(b.r, p.sky, s0, b.n, p.n_max, g.inv_dt, b.f_off,
-                                            reinterpret_cast<DelayRec *>(p.dbuf));
+        k_delays_split<<<grid, 256, 0, s>>>(static_cast<const DF *>(b.r2), p.sky, s0, b.n, p.n_max,
+                                            df_from_double(g.inv_dt), df_from_double(b.f_off),
+                                            b.f_off != 0.0 ? 1 : 0, reinterpret_cast<DelayRec *>(p.dbuf));
         k_geometry<true><<<grid, 256, 0, s>>>(g);
     } else {
         k_delays<<<grid, 256, 0, s>>>(b.r, p.sky, s0, b.n, p.n_max, p.dbuf);
