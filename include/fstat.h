@@ -60,8 +60,10 @@ typedef enum {
 
 typedef enum {
     FSTAT_FP64_PLAIN = 0,    /* every step in FP64, one cell at a time */
-    FSTAT_FP32_BATCHED = 1   /* FP32 resample/FFT/|F|^2, FP64 delay, phase reduction
-                                and compensated sums; many cells per launch */
+    FSTAT_FP32_BATCHED = 1   /* FP32 resample/FFT/|F|^2; the delay in double-float
+                                (~48-bit) and the spindown phase in 64-bit fixed point,
+                                both reduced before any FP32 use; compensated sums;
+                                many cells per launch */
 } fstat_form;
 
 /* One narrow band of one frame (Sect. 2: xdat_d_b.bin + DetSSB.bin). */
