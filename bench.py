@@ -160,10 +160,17 @@ def oracle_rate(w, target_s=30.0):
             break
         grow = min(8.0, max(2.0, target_s / max(el, 1e-3)))
         n = min(w.n_sky * w.n_spin, int(math.ceil(n * grow / threads)) * threads)
+    # one thread: the first sky position's cells, about a second
+    cs1, cp1 = sample_cells(w, w.n_spin)
+    t0 = time.perf_counter()
+    O.cells_F(b, prm, w.alpha, w.delta, w.fdot, cs1, cp1, nthreads=1)
+    el1 = time.perf_counter() - t0
     return {"value": cs.size * nb / el, "unit": UNIT, "cores": threads, "kind": "oracle",
             "sample": f"{cs.size} cells ({len(set(cs.tolist()))} sky positions x up to "
                       f"{w.n_spin} spindowns) of the {w.n_sky}x{w.n_spin} grid, N_fft=2^18, "
-                      f"all {nb} bins, one run of {el:.1f} s"}
+                      f"all {nb} bins, one run of {el:.1f} s",
+            "one_thread": {"value": cs1.size * nb / el1, "unit": UNIT,
+                           "sample": f"{cs1.size} cells of one sky position, one run of {el1:.2f} s"}}
 
 
 # ----------------------------------------------------------------------------- reference arm
