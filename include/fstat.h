@@ -182,7 +182,10 @@ fstat_status fstat_search(fstat_plan *plan, int64_t cell_begin, int64_t cell_end
 /* Copy the candidates of the last search into buf[0 .. cap), sorted by
    (band, sky, spin, bin).  *n_written = min(kept, cap); *n_total = every
    candidate found, including those beyond the device capacity.  Returns
-   FSTAT_ERR_OVERFLOW when *n_total > *n_written.  buf may be NULL when cap = 0. */
+   FSTAT_ERR_OVERFLOW when *n_total > *n_written.  buf may be NULL when cap = 0.
+   More than 65 536 records are sorted on the device (once per search, in a
+   second device buffer the plan allocates on first use: FSTAT_ERR_OOM if it
+   cannot) and read back through pinned host staging that the plan keeps. */
 fstat_status fstat_candidates_get(fstat_plan *plan, fstat_candidate *buf, int64_t cap,
                                   int64_t *n_written, int64_t *n_total);
 
