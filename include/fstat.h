@@ -242,6 +242,48 @@ typedef struct {
 
 fstat_status fstat_plan_autotune(fstat_plan *plan, int64_t sample_cells, fstat_tuning *chosen);
 
+/* The search grid from a lattice generating matrix (Sect. 2: the file grid.bin
+   holds a 4 x 4 matrix M whose rows span the 4-D parameter space; the integer
+   multiples of the rows are the grid points; a sky position is a pair of
+   integers (n, m), a spindown an integer s).  The coordinates of the space are a
+   reading (the paper defers them to a reference not available here), row by row
+   of M: frequency f dt (the FFT's own grid), spindown fdot dt^2 / 2, and the
+   ecliptic-plane components (beta1, beta2) of the unit vector towards the source
+   times f_ref tau_E (tau_E = 1 AU / c = 499.00478 s): the sky point (n, m) is
+   n M[2] + m M[3], it lies on the sphere when beta1^2 + beta2^2 <= 1 (< 1 in the
+   south hemisphere, so points on the ecliptic appear once), and its ecliptic
+   latitude has the hemisphere's sign; spindown s is fdot = 2 s M[1][1] / dt^2.
+   The grid is the product of the sky points and the spindowns, so M must have
+   M[1][2] = M[1][3] = M[2][1] = M[3][1] = 0 (FSTAT_ERR_ARG otherwise). */
+typedef struct {
+    double M[16];               /* row-major; rows: frequency, spindown, sky n, sky m */
+    double dt;                  /* sampling interval, s (> 0) */
+    double f_ref;               /* reference frequency of the sky coordinates, Hz (> 0) */
+    double eps;                 /* obliquity of the ecliptic, rad */
+    int64_t s_lo, s_hi;         /* spindown integers, inclusive */
+    int64_t n_lo, n_hi;         /* sky integers, inclusive (at most 2^20 values each) */
+    int64_t m_lo, m_hi;
+    int32_t hemispheres;        /* 1: north ecliptic hemisphere; 2: north, then south */
+    int32_t reserved_;
+} fstat_lattice;
+
+/* Fills device arrays with the grid of a lattice, ordered by hemisphere, then n,
+   then m (sky) and by s (spindown):
+     alpha, delta  device pointers, cap_sky doubles each (rad, alpha in [0, 2 pi));
+     nm            device pointer to 3 cap_sky int64 (hemisphere 0/1, n, m), or NULL;
+     fdot          device pointer, cap_spin doubles (Hz/s).
+   *n_sky and *n_spin (host) receive the full counts; cap_sky = cap_spin = 0 is a
+   count-only query (the array pointers may then be NULL).  The arrays are ready to
+   pass to fstat_plan_create with inputs_on_device = 1.  Synchronous with respect
+   to the host; allocates and frees a small device buffer of per-block counts.
+   Errors: FSTAT_ERR_ARG (NULL pointer where one is needed, non-finite entry,
+   ranges empty or too large, coupled spindown and sky rows), FSTAT_ERR_OOM,
+   FSTAT_ERR_CUDA, FSTAT_ERR_OVERFLOW (a count exceeds its capacity: the first
+   cap entries are written, the counts stay exact). */
+fstat_status fstat_lattice_grid(const fstat_lattice *lattice, double *alpha, double *delta,
+                                int64_t *nm, int64_t cap_sky, int64_t *n_sky, double *fdot,
+                                int64_t cap_spin, int64_t *n_spin, void *cuda_stream);
+
 /* Allocation-free F of one cell (the paper has no counterpart: this entry point
    exists for callers that cannot allocate device memory -- for example a host
    application that reserves the whole device memory budget up front and hands
@@ -249,13 +291,13 @@ fstat_status fstat_plan_autotune(fstat_plan *plan, int64_t sample_cells, fstat_t
    runs).  It evaluates, without any cudaMalloc, the FP32 zero-padded transforms and
    F = |F_a|^2 norm_a + |F_b|^2 norm_b for every bin in [bin_lo, bin_hi] of one
    (sky, spindown) cell, from the resampled, phase-demodulated series of that sky:
-     w      device pointer, w[4 k .. 4 k + 3] = (Re y_k a_k, Im y_k a_k, Re y_k b_k,
-            Im y_k b_k), k < n (the FP32 form's per-sky series; zero outside the
-            resampled window);
+     w      device pointer, 16-byte aligned, w[4 k .. 4 k + 3] = (Re y_k a_k,
+            Im y_k a_k, Re y_k b_k, Im y_k b_k), k < n (the FP32 form's per-sky
+            series; zero outside the resampled window);
      n_fft  power of two, 2^12 <= n_fft <= 2^18 (the maximum), n_fft >= 2 n;
      chirp_rate  fdot dt^2 / 2 (cycles per sample^2), |chirp_rate| < 1/4;
      norm_a, norm_b  1/(sigma^2 S_aa), 1/(sigma^2 S_bb), >= 0;
-     F_out  device pointer to bin_hi - bin_lo + 1 floats;
+     F_out  device pointer to bin_hi - bin_lo + 1 floats, 4-byte aligned;
      cuda_stream  cudaStream_t or NULL.
    The transforms' intermediate lives in a file-scope device array of
    2 x 2^18 complex floats (4 MiB) and twiddle tables in another (about 20 KiB);
@@ -266,7 +308,10 @@ fstat_status fstat_plan_autotune(fstat_plan *plan, int64_t sample_cells, fstat_t
    call before any stream capture.  Every call shares the arrays and nothing in
    them has to start at zero (each call writes the whole intermediate it reads);
    calls that overlap on the GPU (other streams, other host threads) race on them.
-   Synchronous with respect to the host.  Returns FSTAT_ERR_ARG for a NULL
+   Every call ends by synchronising cuda_stream with the host.  The addresses and
+   the filled-table flags are cached per device for the life of the process: after
+   a cudaDeviceReset of a device the cache is stale, and this entry point must not
+   be called on that device again.  Returns FSTAT_ERR_ARG for a NULL or misaligned
    pointer, a length beyond the maximum or any other invalid argument (nothing is
    launched), FSTAT_ERR_CUDA if a CUDA call fails. */
 fstat_status fstat_cell_F_noalloc(const float *w, int64_t n, int64_t n_fft, double chirp_rate,

@@ -166,7 +166,10 @@ extern "C" fstat_status fstat_cell_F_noalloc(const float *w, int64_t n, int64_t 
     using namespace fstat;
     int lg = 0;
     while ((int64_t(1) << lg) < n_fft) ++lg;
-    if (!w || !F_out || n < 1 || (int64_t(1) << lg) != n_fft || lg < 12 ||
+    // w is read as float4 (16-byte loads) and F_out written as floats: a view that
+    // starts off those boundaries is refused here instead of faulting on the GPU
+    if (!w || !F_out || (reinterpret_cast<uintptr_t>(w) & 15) != 0 ||
+        (reinterpret_cast<uintptr_t>(F_out) & 3) != 0 || n < 1 || (int64_t(1) << lg) != n_fft || lg < 12 ||
         lg > kNoallocMaxLogN || 2 * n > n_fft || bin_lo < 0 || bin_hi < bin_lo || bin_hi >= n_fft ||
         !(norm_a >= 0.0) || !(norm_b >= 0.0))
         return FSTAT_ERR_ARG;

@@ -65,3 +65,32 @@ def test_noalloc_rejects_beyond_maximum():
     assert fs.cell_F_noalloc(buf.data_ptr(), 8, 1 << 19, 0.0, 1.0, 1.0, 1, 7, out.data_ptr()) == fs.FSTAT_ERR_ARG
     assert fs.cell_F_noalloc(buf.data_ptr(), 8, 1 << 11, 0.0, 1.0, 1.0, 1, 7, out.data_ptr()) == fs.FSTAT_ERR_ARG
     assert fs.cell_F_noalloc(0, 8, 1 << 12, 0.0, 1.0, 1.0, 1, 7, out.data_ptr()) == fs.FSTAT_ERR_ARG
+    # views that start off the 16-byte (series) or 4-byte (output) boundary are
+    # refused on the host, before anything is launched
+    assert fs.cell_F_noalloc(buf.data_ptr() + 4, 8, 1 << 12, 0.0, 1.0, 1.0, 1, 7,
+                             out.data_ptr()) == fs.FSTAT_ERR_ARG
+    assert fs.cell_F_noalloc(buf.data_ptr(), 8, 1 << 12, 0.0, 1.0, 1.0, 1, 7,
+                             out.data_ptr() + 2) == fs.FSTAT_ERR_ARG
+
+
+def test_noalloc_allocates_no_device_memory():
+    """The property the entry point exists for: once the kernels of a length are
+    loaded (first call), further calls leave the device's free memory unchanged."""
+    import torch
+    from paper_1410_3677_gb300 import fstat as fs
+    n, n_fft = 3000, 1 << 13
+    rng = np.random.default_rng(7)
+    w = torch.from_numpy(rng.standard_normal((n, 4)).astype(np.float32)).cuda()
+    out = torch.empty(n_fft // 2 - 1, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream().cuda_stream
+    args = (w.data_ptr(), n, n_fft, 1e-7, 1.0, 1.0, 1, n_fft // 2 - 1, out.data_ptr(), stream)
+    assert fs.cell_F_noalloc(*args) == fs.FSTAT_OK     # first call: set-up and module load
+    first = out.clone()                                 # torch's own allocation, outside the window
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    for _ in range(3):
+        assert fs.cell_F_noalloc(*args) == fs.FSTAT_OK
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
+    assert torch.equal(out, first)                      # the shared scratch keeps no state
+    del first
