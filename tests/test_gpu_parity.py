@@ -82,7 +82,12 @@ def test_sky_stage_matches_oracle(fs, form):
     prm = O.params(w.lat, w.gamma, 2, 0.0)
     xu = O.upsample(band.x, 2)
     # a, b: closed forms; y: the band-offset phase 2 pi f_off d (~1e5 rad here)
-    # bounds the FP64 agreement near 1e-11 relative
+    # bounds the FP64 agreement near 1e-11 relative.  FP32 form: a and b are
+    # evaluated in FP32 (absolute error <= tol_ab), so S_aa = sum a^2 over the
+    # window moves by at most 2 tol_ab sum|a| / sum a^2 <= 2 tol_ab / rms(a)
+    # relative (likewise S_bb, and S_ab on the scale sqrt(S_aa S_bb)): 1.4e-5 at the
+    # smallest rms here (rms(a) = 0.29 at sky 7).  tol_S = 1e-5 sits just below that
+    # worst case; through 1/S its effect on F stays 10x below the 1e-4 on F.
     tol_ab, tol_y, tol_S = (1e-12, 1e-10, 1e-12) if form == 0 else (2e-6, 2e-5, 1e-5)
     for sky in (0, 7, 31):
         g = p.debug_sky(0, sky, band.n)
@@ -94,7 +99,8 @@ def test_sky_stage_matches_oracle(fs, form):
         assert ea < tol_ab and eb < tol_ab, (sky, ea, eb)
         ey = np.max(np.abs(g["y"] - r["y"])) / max(1.0, np.max(np.abs(r["y"])))
         assert ey < tol_y, (sky, ey)
-        eS = np.max(np.abs(g["S"] - r["S"]) / np.abs(r["S"]))
+        scale = np.array([r["S"][0], r["S"][1], math.sqrt(r["S"][0] * r["S"][1])])
+        eS = np.max(np.abs(g["S"] - r["S"]) / scale)
         assert eS < tol_S, (sky, g["S"], r["S"])
     p.close()
 
@@ -136,12 +142,13 @@ def _compare_candidates(c, ref, w, form, thr=None):
                                      ref["bin"].tolist()), ref["F"].tolist())}
     gF = {k: f for k, f in zip(zip(c["band"].tolist(), c["sky"].tolist(), c["spin"].tolist(),
                                    c["bin"].tolist()), c["F"].tolist())}
-    for k in kr - kg:     # missed by the GPU: must sit in the band
-        assert abs(2 * refF[k] - thr) <= 2 * tol * max(refF[k], 2.0) * 2, k
-    for k in kg - kr:     # extra on the GPU: its F must be within tolerance of the threshold
-        assert abs(2 * gF[k] - thr) <= 2 * tol * max(gF[k], 2.0) * 2, k
+    for k in kr - kg:     # missed by the GPU: 2F_ref must sit in the band
+        assert abs(2 * refF[k] - thr) <= 2 * tol * max(refF[k], 2.0), k
+    # extra on the GPU: 2F_ref <= thr < 2F_gpu, so with |F_gpu - F_ref| <= tol max(F_ref, 2)
+    # and F_ref < F_gpu, 2F_gpu lies within 2 tol max(F_gpu, 2) above the threshold
+    for k in kg - kr:
+        assert abs(2 * gF[k] - thr) <= 2 * tol * max(gF[k], 2.0), k
     common = kg & kr
-    assert len(common) >= 0.99 * max(len(kr), 1)
     for k in common:
         assert abs(gF[k] - refF[k]) <= tol * max(refF[k], 2.0), k
 
@@ -313,7 +320,7 @@ def test_precision_workload_full_grid_sampled(fs):
         sel = c[(c["sky"] == sk) & (c["spin"] == sp)]
         want = np.nonzero(2 * ref[i] > w.thr_2F)[0] + 1
         got = sel["bin"]
-        band = np.abs(2 * ref[i] - w.thr_2F) <= 2 * 2e-4 * np.maximum(ref[i], 2.0)
+        band = np.abs(2 * ref[i] - w.thr_2F) <= 2 * 1e-4 * np.maximum(ref[i], 2.0)
         sym = set(want.tolist()) ^ set(got.tolist())
         assert all(band[bn - 1] for bn in sym), (sk, sp, sym)
         common = np.intersect1d(want, got)
