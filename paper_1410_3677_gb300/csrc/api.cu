@@ -383,12 +383,17 @@ void create_impl(Plan &p, const fstat_plan_desc *d) {
         if (const char *v = getenv("FSTAT_TMA")) p.tma = atoi(v) != 0;
         if (const char *v = getenv("FSTAT_P2_THREADS")) p.p2_threads = atoi(v) == 128 ? 128 : 256;
         if (const char *v = getenv("FSTAT_FUSED_SLOTS")) p.fused_slots = std::max(2, std::min(256, atoi(v)));
-        if (const char *v = getenv("FSTAT_FUSED_AHEAD")) p.fused_ahead = std::max(1, std::min(p.fused_slots - 1, atoi(v)));
+        if (const char *v = getenv("FSTAT_FUSED_AHEAD")) p.fused_ahead = std::max(1, atoi(v));
+        p.fused_ahead = std::min(p.fused_ahead, p.fused_slots - 1);
         if (const char *v = getenv("FSTAT_FUSED_TPI")) {
             int t = 1;
             while (2 * t <= std::min(64, atoi(v))) t *= 2;
             p.fused_tpi = t;
         }
+        // the fused launch needs no scratch per cell (a ring of slots): one launch
+        // per sky batch
+        p.fused_batch = std::max<int64_t>(1, std::min<int64_t>(65535, p.sky_batch * d->n_spin));
+        if (const char *v = getenv("FSTAT_FUSED_BATCH")) p.fused_batch = std::max(1, std::min(65535, atoi(v)));
     }
     p.slot_cells = (size_t)std::max<int64_t>(p.cell_batch, fp32 ? p.fused_slots : 1);
     size_t scratch_bytes = std::max<size_t>((size_t)p.n_workers * p.slot_cells * 2 * max_nfft * tsz,
@@ -405,7 +410,8 @@ void create_impl(Plan &p, const fstat_plan_desc *d) {
         if (const char *v = getenv("FSTAT_PERSISTENT")) p.use_persistent = atoi(v) != 0;
         if (const char *v = getenv("FSTAT_ELEMS_PER_THREAD")) p.elems_per_thread = atoi(v) == 8 ? 8 : 16;
         if (const char *v = getenv("FSTAT_ENGINE")) p.engine = atoi(v) == 1 ? 1 : 2;
-        p.fctl = dalloc<uint32_t>(p, (size_t)p.n_workers * (1 + 2 * (size_t)p.cell_batch), n_alloc);
+        p.fctl = dalloc<uint32_t>(p, (size_t)p.n_workers * (1 + 2 * (size_t)std::max(p.cell_batch, p.fused_batch)),
+                                  n_alloc);
     }
     p.scratch = dalloc<unsigned char>(p, scratch_bytes, n_alloc);
     p.bw_elems = 2 * p.n_max + 2 * max_m;
@@ -547,7 +553,7 @@ void enqueue_search(Plan &p, int64_t begin, int64_t end) {
     const int64_t per_band = d.n_sky * d.n_spin;
     const int NW = (int)p.workers.size();
     const size_t slot_bytes = p.slot_cells * 2 * (size_t)p.n_fft_max * (fp32 ? 8 : 16);
-    const size_t ctl_words = 1 + 2 * (size_t)p.cell_batch;
+    const size_t ctl_words = 1 + 2 * (size_t)std::max(p.cell_batch, p.fused_batch);
     // the plan's stream waits for every worker stream
     auto join_workers = [&]() {
         if (NW < 2) return;
@@ -619,10 +625,11 @@ void enqueue_search(Plan &p, int64_t begin, int64_t end) {
                     check(cudaStreamWaitEvent(p.workers[i], p.ev_geo[par], 0), "stream wait");
             }
             const bool fused = fp32 && fused_supported(p, b.logn);
-            for (int64_t c = c_lo; c < c_hi; c += p.cell_batch, ++cbi) {
+            const int64_t batch = fused ? p.fused_batch : p.cell_batch;
+            for (int64_t c = c_lo; c < c_hi; c += batch, ++cbi) {
                 const int wi = (int)(cbi % NW);
                 cudaStream_t ws = p.workers[wi];
-                const int64_t nc = std::min<int64_t>(p.cell_batch, c_hi - c);
+                const int64_t nc = std::min<int64_t>(batch, c_hi - c);
                 CellBufs cbuf{p.wbuf[par], p.normbuf[par],
                               static_cast<unsigned char *>(p.scratch) + wi * slot_bytes};
                 if (fused) {

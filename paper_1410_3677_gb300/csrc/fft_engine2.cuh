@@ -281,6 +281,12 @@ struct LoaderStaged { static constexpr bool value = false; };
 template <class LD>
 struct LoaderStaged<LD, decltype(void(LD::kStaged))> { static constexpr bool value = LD::kStaged; };
 
+// Called by run_pass once this thread has issued the loads of its stage-0 inputs
+// (work that may wait on memory, placed where the thread waits for its loads anyway).
+struct NoHook {
+    __device__ __forceinline__ void after_loads() const {}
+};
+
 // ZQ: the stage-0 inputs r >= R0 ZQ/8 (sequence elements >= M ZQ/8) are known
 // to be zero (the zero padding of a transform at least 8/ZQ times the series):
 // the loader is asked for R0 ZQ/8 elements and the first DFT skips the zeros
@@ -291,8 +297,8 @@ struct LoaderStaged<LD, decltype(void(LD::kStaged))> { static constexpr bool val
 // half-warp reading 16 consecutive j); else tw is the table W_M^m, m < M, from
 // which the power-of-two rows are staged in shared memory.
 template <typename T, int M, int SEQ, int EH, int DIR, int MAPM, class LD, class ST, int ZQ = 8,
-          bool TWFULL = false>
-__device__ __forceinline__ void run_pass(LD &ld, ST &st, const T *__restrict__ tw) {
+          bool TWFULL = false, class HK = NoHook>
+__device__ __forceinline__ void run_pass(LD &ld, ST &st, const T *__restrict__ tw, const HK &hk = HK{}) {
     using V = typename Vec2T<T>::type;
     constexpr int R0 = radix0(M), R1 = radix1(M);
     constexpr int TPF = M / EH;
@@ -329,6 +335,7 @@ __device__ __forceinline__ void run_pass(LD &ld, ST &st, const T *__restrict__ t
     constexpr int RL0 = R0 * ZQ / 8;   // stage-0 inputs that can be non-zero
 #pragma unroll
     for (int i = 0; i < NJ0; ++i) ld.template load<RL0, JPF0>(job<MAPM, SEQ, TPF, THREADS>(i), &re[i * R0], &im[i * R0]);
+    hk.after_loads();
 #pragma unroll
     for (int i = 0; i < NJ0; ++i) {
         if constexpr (ZQ < 8) dft_half_zero<R0, DIR, RL0>(&re[i * R0], &im[i * R0]);

@@ -128,7 +128,8 @@ struct Plan {
     uint32_t *fctl = nullptr;      // per worker: 1 + 2 * cell_batch counters of the fused launch
     size_t slot_cells = 0;         // cells of scratch per worker (>= cell_batch, >= the fused ring)
     int fused_slots = kFusedSlots, fused_ahead = kFusedAhead;
-    int fused_tpi = 4;             // tiles per ticket of the fused launch (power of two)
+    int fused_tpi = 1;             // tiles per ticket of the fused launch (power of two)
+    int64_t fused_batch = 1;       // cells per fused launch (a sky batch)
     int64_t pf_dist = 0;           // two-stage pass 2: L2 prefetch distance in CTAs (0: off)
     bool tma = true;               // two-stage pass 2: rows staged by bulk copies
     int p2_threads = 128;          // two-stage pass 2 with bulk copies: CTA size 256 or 128

@@ -554,19 +554,32 @@ k_pass2_ib(LD ld, SearchEpi2<Cfg2<LOGN, 2, TS>, false> ep, const float *__restri
 }
 
 // ------------------------------------------------------------------ fused launch
-// Both passes of a batch of cells in one launch.  Every CTA takes the next item
-// from a ticket counter; items run in the order
-//   step s: the T1 pass-1 tiles of cell s, then the T2 pass-2 tiles of cell s - A
-// (A = ahead), so pass 2 of a cell starts A cells after its pass 1 and the
-// cell's intermediate is still in L2.  Cells use a ring of S > A scratch slots
-// (4 MiB each at N = 2^18, resident in L2).  Pass 2 of cell c waits for the T1
-// pass-1 tiles of c; pass 1 of cell c waits until pass 2 of cell c - S has
-// released the slot.  A CTA publishes its completion the way a grid-wide
-// barrier does: CTA barrier, then one thread's fence and release increment.  Both waited-on items carry smaller tickets than the
-// waiter, so they belong to CTAs already running, whatever the order in which
-// the hardware starts CTAs: every wait ends.  Waits are still bounded (1 s of
-// global time); one that runs out sets the error flag, and every later wait
-// sees the flag and gives up at once.
+// Both passes of a batch of cells in one persistent launch fed by a device work
+// queue (a ticket counter).  Items run in the order
+//   step s: the I1 pass-1 items of cell s, then the I2 pass-2 items of cell s - A
+// (A = ahead; an item is tpi tiles), so pass 2 of a cell starts A cells after its
+// pass 1 and the cell's intermediate is still in L2.  Cells use a ring of S > A
+// scratch slots (4 MiB each at N = 2^18, resident in L2).  Pass 2 of cell c needs
+// the T1 pass-1 tiles of c; pass 1 of cell c reuses the slot of cell c - S and
+// needs the T2 pass-2 tiles of that cell.  Every waited-on item carries a smaller
+// ticket than the waiter, so it belongs to a CTA that is already running whatever
+// order the hardware starts CTAs in, and every wait ends; waits are still bounded
+// (1 s of global time), and one that runs out sets the error flag, which makes
+// every later wait give up at once.
+//
+// The per-item protocol keeps the CTA's warps computing:
+//  - thread 0 claims the next ticket when an item starts and reads the answer
+//    when it ends, so the atomic's round trip runs under the item;
+//  - at the end of an item thread 0 looks once (acquire load) at the next
+//    item's dependency and hands the ticket to the CTA through shared memory at
+//    the one CTA barrier per item;
+//  - an item's completion is published (release fence, counter increment by
+//    thread 0, covering the whole CTA's stores through that barrier) only after
+//    the next item's loads are issued, where the fence's wait for the stores
+//    overlaps the wait for those loads;
+//  - when the look finds the dependency unmet (rare), thread 0 first publishes
+//    the item it still holds (a waiter must never hold an unpublished item that
+//    its own wait needs), then waits, behind one more barrier.
 struct FusedCtl {
     uint32_t *ticket;   // next item
     uint32_t *done1;    // [nc] pass-1 tiles finished per cell
@@ -592,75 +605,159 @@ __device__ __forceinline__ bool fused_wait(const uint32_t *cnt, uint32_t target,
     }
 }
 
-// Persistent: the grid holds as many CTAs as fit on the GPU, each looping over
-// tickets; the next ticket is claimed while the current item runs, so its
-// latency is hidden.  A CTA holding a claimed ticket is running, which keeps the
-// argument above valid.
+// Release of one finished item: the CTA barrier before this call orders every
+// thread's stores of the item before thread 0's fence.
+__device__ __forceinline__ void fused_publish(uint32_t *cnt, uint32_t add) {
+    __threadfence();
+    atomicAdd(cnt, add);
+}
+
+// thread 0's hook inside run_pass, once its loads of the current item are
+// issued (the waits below then overlap the wait for those loads): publishes the
+// previous item and claims the ticket of the next one.
+struct PublishHook {
+    uint32_t *cnt;      // nullptr: nothing held
+    uint32_t add;
+    uint32_t *ticket;   // nullptr: no claim here
+    uint32_t *next;     // shared-memory word that receives the claimed ticket
+    __device__ __forceinline__ void after_loads() const {
+        if (cnt) fused_publish(cnt, add);
+        if (ticket) *next = atomicAdd(ticket, 1u);
+    }
+};
+
+// An item's cell, pass and tile, and the counter it waits for (nullptr: none).
+struct FusedItem {
+    int64_t cell, slot;
+    int tile;           // first tile of the item within its pass
+    bool p1, valid;
+    const uint32_t *dep;
+    uint32_t target;
+};
+
+template <int T1, int T2>
+__device__ __forceinline__ FusedItem fused_decode(uint32_t item, const FusedCtl &ctl) {
+    const uint32_t I1 = (uint32_t)(T1 / ctl.tpi), I2 = (uint32_t)(T2 / ctl.tpi);
+    const uint32_t step = item / (I1 + I2);
+    const uint32_t r = item - step * (I1 + I2);
+    FusedItem f;
+    f.p1 = r < I1;
+    f.cell = f.p1 ? (int64_t)step : (int64_t)step - ctl.ahead;
+    f.valid = f.cell >= 0 && f.cell < ctl.nc;
+    f.slot = f.valid ? (int64_t)((uint32_t)f.cell % (uint32_t)ctl.slots) : 0;
+    f.tile = (int)(f.p1 ? r : r - I1) * ctl.tpi;
+    f.dep = nullptr;
+    f.target = 0;
+    if (f.valid) {
+        if (!f.p1) { f.dep = ctl.done1 + f.cell; f.target = T1; }
+        else if (f.cell >= ctl.slots) { f.dep = ctl.done2 + (f.cell - ctl.slots); f.target = T2; }
+    }
+    return f;
+}
+
+// One tile of each pass, kept out of line: the persistent loop's own state then
+// costs the passes no registers (inlined, the two passes and the loop spill).
+template <int LOGN, int Z1>
+__device__ __noinline__ void fused_tile1(const SearchLoad2<Cfg2<LOGN, 1>> *pl, const ScratchStore2<Cfg2<LOGN, 1>> *po,
+                                         const float *__restrict__ tw, int tile, int64_t cell, int64_t slot,
+                                         PublishHook hk) {
+    using C1 = Cfg2<LOGN, 1>;
+    SearchLoad2<C1> l = *pl;
+    ScratchStore2<C1> o = *po;
+    l.init(tile, cell, slot);
+    o.init(tile, cell, slot);
+    eng2::run_pass<float, C1::M, C1::SEQ, C1::EH, -1, eng2::kMapFJ, SearchLoad2<C1>, ScratchStore2<C1>, Z1, true,
+                   PublishHook>(l, o, tw, hk);
+}
+
 template <int LOGN, bool LOWER>
+__device__ __noinline__ void fused_tile2(const ScratchLoad2<Cfg2<LOGN, 2>> *pl,
+                                         const SearchEpi2<Cfg2<LOGN, 2>, LOWER> *po, const float *__restrict__ tw,
+                                         int tile, int64_t cell, int64_t slot, PublishHook hk) {
+    using C2 = Cfg2<LOGN, 2>;
+    ScratchLoad2<C2> l = *pl;
+    SearchEpi2<C2, LOWER> o = *po;
+    l.init(tile, cell, slot);
+    o.init(tile, cell, slot);
+    eng2::run_pass<float, C2::M, C2::SEQ, C2::EH, -1, eng2::kMapW, ScratchLoad2<C2>, SearchEpi2<C2, LOWER>, 8, true,
+                   PublishHook>(l, o, tw, hk);
+}
+
+// Persistent: the grid holds as many CTAs as fit on the GPU at once.  The loop's
+// state lives in shared memory and is re-read after each tile, so nothing but
+// the item counter is live across the out-of-line tiles.
+template <int LOGN, bool LOWER, int Z1>
 __global__ void __launch_bounds__(256, 3)
-k_search_fused(SearchLoad2<Cfg2<LOGN, 1>> ld1, ScratchStore2<Cfg2<LOGN, 1>> st1,
-               ScratchLoad2<Cfg2<LOGN, 2>> ld2, SearchEpi2<Cfg2<LOGN, 2>, LOWER> st2,
-               const float *__restrict__ tw_s1, const float *__restrict__ tw_s2, FusedCtl ctl) {
+k_search_fused(const __grid_constant__ SearchLoad2<Cfg2<LOGN, 1>> ld1,
+               const __grid_constant__ ScratchStore2<Cfg2<LOGN, 1>> st1,
+               const __grid_constant__ ScratchLoad2<Cfg2<LOGN, 2>> ld2,
+               const __grid_constant__ SearchEpi2<Cfg2<LOGN, 2>, LOWER> st2,
+               const float *__restrict__ tw_s1, const float *__restrict__ tw_s2, const FusedCtl ctl) {
     using C1 = Cfg2<LOGN, 1>;
     using C2 = Cfg2<LOGN, 2>;
     constexpr int T1 = C1::TILES, T2 = C2::TILES;
-    const int tpi = ctl.tpi;
-    const int I1 = T1 / tpi, I2 = T2 / tpi;          // items per cell and pass
-    const int64_t total = (ctl.nc + ctl.ahead) * (int64_t)(I1 + I2);
-    __shared__ uint32_t s_item, s_next;
-    __shared__ int s_go;
-    if (threadIdx.x == 0) s_item = atomicAdd(ctl.ticket, 1u);
-    __syncthreads();
-    for (;;) {
-        const int64_t item = s_item;
-        if (item >= total) return;                   // the same for the whole CTA
-        const int64_t step = item / (I1 + I2);
-        const int r = (int)(item - step * (I1 + I2));
-        const bool p1 = r < I1;
-        const int64_t cell = p1 ? step : step - ctl.ahead;
-        const bool valid = cell >= 0 && cell < ctl.nc;
-        const int64_t slot = valid ? cell % ctl.slots : 0;
-        if (threadIdx.x == 0) {
-            s_next = atomicAdd(ctl.ticket, 1u);
-            bool ok = true;
-            if (valid) {
-                if (!p1) ok = fused_wait(ctl.done1 + cell, T1, ctl.err);
-                else if (cell >= ctl.slots) ok = fused_wait(ctl.done2 + (cell - ctl.slots), T2, ctl.err);
-            }
-            s_go = !ok ? -1 : (valid ? 1 : 0);
-        }
-        __syncthreads();
-        const int go = s_go;
-        if (go < 0) return;                          // a wait gave up: every later wait will too
-        if (go) {
-            if (p1) {
-#pragma unroll 1
-                for (int u = 0; u < tpi; ++u) {
-                    if (u) __syncthreads();              // the previous tile's exchange is read
-                    ld1.init(r * tpi + u, cell, slot);
-                    st1.init(r * tpi + u, cell, slot);
-                    eng2::run_pass<float, C1::M, C1::SEQ, C1::EH, -1, eng2::kMapFJ, SearchLoad2<C1>,
-                                   ScratchStore2<C1>, 4, true>(ld1, st1, tw_s2);
-                }
-            } else {
-#pragma unroll 1
-                for (int u = 0; u < tpi; ++u) {
-                    if (u) __syncthreads();
-                    ld2.init((r - I1) * tpi + u, cell, slot);
-                    st2.init((r - I1) * tpi + u, cell, slot);
-                    eng2::run_pass<float, C2::M, C2::SEQ, C2::EH, -1, eng2::kMapW, ScratchLoad2<C2>,
-                                   SearchEpi2<C2, LOWER>, 8, true>(ld2, st2, tw_s1);
-                }
-            }
-            __syncthreads();
-            if (threadIdx.x == 0 && !(p1 && cell == ctl.withhold)) {
-                __threadfence();
-                ptx::red_release_add(p1 ? ctl.done1 + cell : ctl.done2 + cell, (uint32_t)tpi);
-            }
-        }
-        if (threadIdx.x == 0) s_item = s_next;
-        __syncthreads();
+    __shared__ uint32_t s_item[2];
+    __shared__ int s_wait[2];
+    __shared__ int s_fail;
+    __shared__ uint32_t *s_held;         // thread 0: counter of the finished, unpublished item
+    __shared__ uint32_t s_nxt;           // thread 0: the ticket claimed while the item runs
+    const bool t0 = threadIdx.x == 0;
+    auto total = [&]() {                 // < 2^32: checked by the host
+        return (uint32_t)(ctl.nc + ctl.ahead) * (uint32_t)(T1 / ctl.tpi + T2 / ctl.tpi);
+    };
+    if (t0) {
+        s_item[0] = atomicAdd(ctl.ticket, 1u);
+        s_wait[0] = 1;                   // the first item's dependency: waited for below
+        s_fail = 0;
+        s_held = nullptr;
     }
+    __syncthreads();
+    for (int k = 0;; ++k) {
+        {
+            const uint32_t item = s_item[k & 1];
+            if (item >= total()) break;  // the same for the whole CTA
+            if (s_wait[k & 1]) {         // publish what is held, then wait
+                if (t0) {
+                    if (s_held) fused_publish(s_held, (uint32_t)ctl.tpi);
+                    s_held = nullptr;
+                    const FusedItem f = fused_decode<T1, T2>(item, ctl);
+                    if (f.dep && !fused_wait(f.dep, f.target, ctl.err)) s_fail = 1;
+                }
+                __syncthreads();
+                if (s_fail) return;
+            }
+        }
+        for (int u = 0; u < ctl.tpi; ++u) {
+            const FusedItem f = fused_decode<T1, T2>(s_item[k & 1], ctl);
+            if (!f.valid) break;
+            if (u) __syncthreads();      // the previous tile's exchange has been read
+            const bool first = t0 && u == 0;
+            const PublishHook h{first ? s_held : nullptr, (uint32_t)ctl.tpi, first ? ctl.ticket : nullptr,
+                                &s_nxt};
+            if (f.p1) fused_tile1<LOGN, Z1>(&ld1, &st1, tw_s2, f.tile + u, f.cell, f.slot, h);
+            else fused_tile2<LOGN, LOWER>(&ld2, &st2, tw_s1, f.tile + u, f.cell, f.slot, h);
+            if (first) s_held = nullptr;
+        }
+        if (t0) {
+            const FusedItem f = fused_decode<T1, T2>(s_item[k & 1], ctl);
+            if (!f.valid) {              // an empty item ran no hook
+                if (s_held) fused_publish(s_held, (uint32_t)ctl.tpi);
+                s_nxt = atomicAdd(ctl.ticket, 1u);
+            }
+            s_held = f.valid && !(f.p1 && f.cell == ctl.withhold) ? (f.p1 ? ctl.done1 : ctl.done2) + f.cell
+                                                                  : nullptr;
+            const uint32_t nxt = s_nxt;
+            int wait = 0;
+            if (nxt < total()) {         // one look at the next item's dependency
+                const FusedItem g = fused_decode<T1, T2>(nxt, ctl);
+                if (g.dep && ptx::ld_acquire(g.dep) < g.target) wait = 1;
+            }
+            s_item[(k + 1) & 1] = nxt;
+            s_wait[(k + 1) & 1] = wait;
+        }
+        __syncthreads();                 // every thread's stores of the item; the next ticket
+    }
+    if (t0 && s_held) fused_publish(s_held, (uint32_t)ctl.tpi);
 }
 
 }  // namespace fstat

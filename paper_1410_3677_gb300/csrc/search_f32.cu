@@ -97,18 +97,22 @@ int launch_fused(const Plan &p, int band_idx, const BandDev &b, int64_t s0, int6
     const int tpi = std::min(p.fused_tpi, std::min(C1::TILES, C2::TILES));
     FusedCtl ctl{cb.ctl, cb.ctl + 1, cb.ctl + 1 + nc, p.qerr, nc, p.fused_slots, p.fused_ahead, tpi, wh};
     constexpr size_t smem = C1::SMEM > C2::SMEM ? C1::SMEM : C2::SMEM;
-    auto k = k_search_fused<LOGN, LOWER>;
-    static int resident = 0;   // CTAs of this kernel that fit on the device at once
-    if (!resident) {
+    // pass-1 columns known zero beyond 3/8 of their length (radix-32 first stage) or 1/2
+    const bool z3 = eng2::radix0(C1::M) == 32 && 8 * b.n <= 3 * (int64_t)C1::N;
+    auto k = z3 ? k_search_fused<LOGN, LOWER, eng2::radix0(C1::M) == 32 ? 3 : 4>
+                : k_search_fused<LOGN, LOWER, 4>;
+    static int resident[2] = {0, 0};   // CTAs of each variant that fit on the device at once
+    int &res = resident[z3 ? 1 : 0];
+    if (!res) {
         set_smem(k, smem);
         int dev = 0, sms = 0, per_sm = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, 256, smem);
-        resident = std::max(1, sms * std::max(per_sm, 1));
+        res = std::max(1, sms * std::max(per_sm, 1));
     }
     const int64_t items = (nc + p.fused_ahead) * (int64_t)(C1::TILES / tpi + C2::TILES / tpi);
-    const unsigned grid = (unsigned)std::min<int64_t>(items, resident);
+    const unsigned grid = (unsigned)std::min<int64_t>(items, res);
     k<<<grid, 256, smem, s>>>(ld1, st1, ld2, st2, tw->s1_f, tw->s2_f, ctl);
     return 1;
 }

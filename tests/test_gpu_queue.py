@@ -62,8 +62,10 @@ FUSED = {"FSTAT_PERSISTENT": "0", "FSTAT_FUSED": "1"}    # two-stage engine, one
     (TWO, {"FSTAT_PF_DIST": "0", "FSTAT_CELL_BATCH": "9"}),
     (TWO, {"FSTAT_CELL_BATCH": "5", "FSTAT_STREAMS": "2"}),
     (TWO, FUSED),
-    (TWO, {"FSTAT_FUSED": "1", "FSTAT_CELL_BATCH": "3"}),
-    (TWO, {"FSTAT_FUSED": "1", "FSTAT_CELL_BATCH": "11", "FSTAT_STREAMS": "2"}),
+    (TWO, {"FSTAT_FUSED": "1", "FSTAT_FUSED_BATCH": "3"}),
+    (TWO, {"FSTAT_FUSED": "1", "FSTAT_FUSED_BATCH": "11", "FSTAT_STREAMS": "2"}),
+    (TWO, {"FSTAT_FUSED": "1", "FSTAT_FUSED_TPI": "2", "FSTAT_FUSED_SLOTS": "3", "FSTAT_FUSED_AHEAD": "2"}),
+    (TWO, {"FSTAT_FUSED": "1", "FSTAT_FUSED_TPI": "4", "FSTAT_FUSED_BATCH": "5"}),
 ])
 def test_launch_shapes_match_bitwise(fs, base, env):
     """The queue-fed persistent kernel, the fused ticket-ordered launch and other
