@@ -85,6 +85,9 @@ def lib():
         L.orc_search.restype = i64
         L.orc_cells_F.argtypes = [P(OrcBand), P(OrcParams), dp, dp, dp, P(i64), P(i64), i64,
                                   i64, i64, i32, dp]
+        L.orc_lattice_spin.argtypes = [dp, f64, i64, i64, dp]
+        L.orc_lattice_sky.argtypes = [dp, f64, f64, i64, i64, i64, i64, i32, dp, dp, P(i64), i64,
+                                      P(i64)]
         _lib = L
     return _lib
 
@@ -233,3 +236,27 @@ def cells_F(band, prm, alpha, delta, fdot, cells_sky, cells_spin, bin_lo=0, bin_
                              cs.ctypes.data_as(P(i64)), cp.ctypes.data_as(P(i64)), cs.size, lo,
                              hi, nthreads, _dp(F)), "cells_F")
     return F
+
+
+# ----------------------------------------------------------------------- grid from M
+def lattice_spin(M, dt, s_lo, s_hi):
+    """fdot of the spindown integers s_lo..s_hi (the spindown row of M)."""
+    M = _f64(np.asarray(M).reshape(16))
+    out = np.empty(s_hi - s_lo + 1)
+    _check(lib().orc_lattice_spin(_dp(M), float(dt), s_lo, s_hi, _dp(out)), "lattice_spin")
+    return out
+
+
+def lattice_sky(M, f_ref, eps, n_lo, n_hi, m_lo, m_hi, hemispheres=1):
+    """Sky points of the lattice on the sphere: (alpha, delta, nm[:, (hemisphere, n, m)])."""
+    M = _f64(np.asarray(M).reshape(16))
+    cnt = i64()
+    _check(lib().orc_lattice_sky(_dp(M), float(f_ref), float(eps), n_lo, n_hi, m_lo, m_hi,
+                                 hemispheres, None, None, None, 0, C.byref(cnt)), "lattice_sky")
+    n = cnt.value
+    a, d = np.empty(n), np.empty(n)
+    nm = np.empty((n, 3), np.int64)
+    _check(lib().orc_lattice_sky(_dp(M), float(f_ref), float(eps), n_lo, n_hi, m_lo, m_hi,
+                                 hemispheres, _dp(a), _dp(d), nm.ctypes.data_as(P(i64)), n,
+                                 C.byref(cnt)), "lattice_sky")
+    return a, d, nm

@@ -574,3 +574,71 @@ int orc_cells_F(const orc_band *band_in, const orc_params *p, const double *alph
     free(wa); free(th); free(xu);
     return rc;
 }
+
+/* ---- grid from the generating matrix (Sect. 2, grid.bin) ------------------- */
+/* The paper: the rows of the 4 x 4 matrix M span the 4-D parameter space and the
+   integer multiples of the rows are the grid points; a sky position is a pair of
+   integers (n, m), a spindown an integer s.  Coordinates of the space (a reading:
+   the reference that defines them is not available):
+     w0 = f dt                 frequency, cycles per sample (the FFT's own grid)
+     w1 = fdot dt^2 / 2        spindown, cycles per sample^2 (the phase w1 k^2)
+     w2 = f_ref tau_E beta1    sky: the ecliptic-plane components (beta1, beta2)
+     w3 = f_ref tau_E beta2    of the unit vector towards the source, in cycles of
+                               the orbital Roemer phase at the reference frequency
+   with tau_E = 1 AU / c.  Grid point (s, n, m) = s M[1] + n M[2] + m M[3]
+   (rows 0..3 = frequency, spindown, sky n, sky m).  A sky point lies on the
+   sphere when beta1^2 + beta2^2 <= 1; the ecliptic latitude's sign is the
+   hemisphere (points on the ecliptic belong to the north one). */
+#define TAU_E_S 499.00478383615643   /* 1 AU / c, s */
+
+int orc_lattice_spin(const double *M, double dt, int64_t s_lo, int64_t s_hi, double *fdot) {
+    if (!M || !fdot || !(dt > 0) || s_hi < s_lo) return -1;
+    for (int64_t s = s_lo; s <= s_hi; ++s) {
+        const double w1 = (double)s * M[4 + 1];
+        fdot[s - s_lo] = 2.0 * w1 / (dt * dt);
+    }
+    return 0;
+}
+
+/* Equatorial (alpha, delta) of the unit vector with ecliptic components
+   (beta1, beta2, h sqrt(1 - beta1^2 - beta2^2)). */
+static void ecl_to_equ(double b1, double b2, double h, double eps, double *alpha, double *delta) {
+    double q = 1.0 - b1 * b1 - b2 * b2;
+    if (q < 0.0) q = 0.0;
+    const double ze = h * sqrt(q);
+    const double x = b1;
+    const double y = b2 * cos(eps) - ze * sin(eps);
+    const double z = b2 * sin(eps) + ze * cos(eps);
+    double a = atan2(y, x);
+    if (a < 0.0) a += TWO_PI;
+    *alpha = a;
+    *delta = asin(z > 1.0 ? 1.0 : (z < -1.0 ? -1.0 : z));
+}
+
+int orc_lattice_sky(const double *M, double f_ref, double eps, int64_t n_lo, int64_t n_hi,
+                    int64_t m_lo, int64_t m_hi, int hemispheres, double *alpha, double *delta,
+                    int64_t *nm, int64_t cap, int64_t *count) {
+    if (!M || !count || !(f_ref > 0) || n_hi < n_lo || m_hi < m_lo ||
+        (hemispheres != 1 && hemispheres != 2))
+        return -1;
+    const double scale = f_ref * TAU_E_S;
+    int64_t c = 0;
+    for (int hs = 0; hs < hemispheres; ++hs) {
+        const double h = hs == 0 ? 1.0 : -1.0;
+        for (int64_t n = n_lo; n <= n_hi; ++n)
+            for (int64_t m = m_lo; m <= m_hi; ++m) {
+                const double w2 = (double)n * M[8 + 2] + (double)m * M[12 + 2];
+                const double w3 = (double)n * M[8 + 3] + (double)m * M[12 + 3];
+                const double b1 = w2 / scale, b2 = w3 / scale;
+                const double r2 = b1 * b1 + b2 * b2;
+                if (hs == 0 ? !(r2 <= 1.0) : !(r2 < 1.0)) continue;
+                if (c < cap) {
+                    if (alpha && delta) ecl_to_equ(b1, b2, h, eps, &alpha[c], &delta[c]);
+                    if (nm) { nm[3 * c] = hs; nm[3 * c + 1] = n; nm[3 * c + 2] = m; }
+                }
+                ++c;
+            }
+    }
+    *count = c;
+    return 0;
+}

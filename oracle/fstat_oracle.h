@@ -123,6 +123,21 @@ int orc_cells_F(const orc_band *band, const orc_params *p, const double *alpha,
                 const int64_t *cells_spin, int64_t n_cells, int64_t bin_lo,
                 int64_t bin_hi, int nthreads, double *F);
 
+/* ---- grid from the generating matrix M (Sect. 2, grid.bin) ---------------- */
+/* M: 4 x 4 row-major, rows = frequency, spindown, sky n, sky m directions in the
+   coordinates (f dt, fdot dt^2/2, f_ref tau_E beta1, f_ref tau_E beta2), beta the
+   ecliptic-plane components of the unit vector towards the source, tau_E = 1 AU/c.
+   orc_lattice_spin: fdot[s - s_lo] of the spindown integers s_lo..s_hi from the
+   spindown row alone.  orc_lattice_sky: the sky points (n, m) of [n_lo, n_hi] x
+   [m_lo, m_hi] that lie on the sphere, north ecliptic hemisphere first (then the
+   south one when hemispheres = 2), n then m ascending; alpha, delta (rad) and
+   nm[3 c .. 3 c + 2] = (hemisphere 0/1, n, m) of the first cap points; *count =
+   all points. */
+int orc_lattice_spin(const double *M, double dt, int64_t s_lo, int64_t s_hi, double *fdot);
+int orc_lattice_sky(const double *M, double f_ref, double eps, int64_t n_lo, int64_t n_hi,
+                    int64_t m_lo, int64_t m_hi, int hemispheres, double *alpha, double *delta,
+                    int64_t *nm, int64_t cap, int64_t *count);
+
 #ifdef __cplusplus
 }
 #endif
