@@ -61,6 +61,12 @@ class fstat_tuning(C.Structure):
                 ("cells_per_launch", i64), ("ms_per_cell", f64)]
 
 
+class fstat_lattice(C.Structure):
+    _fields_ = [("M", f64 * 16), ("dt", f64), ("f_ref", f64), ("eps", f64), ("s_lo", i64),
+                ("s_hi", i64), ("n_lo", i64), ("n_hi", i64), ("m_lo", i64), ("m_hi", i64),
+                ("hemispheres", i32), ("reserved_", i32)]
+
+
 class fstat_plan_info(C.Structure):
     _fields_ = [("n_cells", i64), ("f_evals", i64), ("device_bytes", i64),
                 ("kernel_launches", i64), ("n_fft_max", i64)]
@@ -94,6 +100,9 @@ _lib.fstat_plan_autotune.restype = i32
 _lib.fstat_cell_F_noalloc.argtypes = [C.c_void_p, i64, i64, f64, f64, f64, i64, i64,
                                        C.c_void_p, C.c_void_p]
 _lib.fstat_cell_F_noalloc.restype = i32
+_lib.fstat_lattice_grid.argtypes = [P(fstat_lattice), C.c_void_p, C.c_void_p, C.c_void_p, i64, P(i64),
+                                    C.c_void_p, i64, P(i64), C.c_void_p]
+_lib.fstat_lattice_grid.restype = i32
 _lib.fstat_measure_fp32_fma.argtypes = [P(f64), C.c_void_p]
 _lib.fstat_measure_fp32_fma.restype = i32
 _lib.fstat_measure_l2_copy.argtypes = [i64, P(f64), C.c_void_p]
@@ -344,6 +353,51 @@ def cell_F_noalloc(w_dev_ptr: int, n: int, n_fft: int, chirp_rate: float, norm_a
     return _lib.fstat_cell_F_noalloc(C.c_void_p(w_dev_ptr), int(n), int(n_fft), float(chirp_rate),
                                      float(norm_a), float(norm_b), int(bin_lo), int(bin_hi),
                                      C.c_void_p(F_out_dev_ptr), C.c_void_p(stream) if stream else None)
+
+
+def lattice_grid(M, dt: float, f_ref: float, eps: float, s_range, n_range, m_range,
+                 hemispheres: int = 1, stream: Optional[int] = None):
+    """fstat_lattice_grid: the search grid of a generating matrix M (4 x 4, rows
+    frequency, spindown, sky n, sky m) over inclusive integer ranges, as torch CUDA
+    tensors (alpha, delta, nm[:, (hemisphere, n, m)], fdot), ready for
+    Plan(..., on_device=True)."""
+    import torch
+    L = fstat_lattice()
+    Mf = np.ascontiguousarray(np.asarray(M, np.float64).reshape(16))
+    for i in range(16):
+        L.M[i] = float(Mf[i])
+    L.dt, L.f_ref, L.eps = float(dt), float(f_ref), float(eps)
+    L.s_lo, L.s_hi = int(s_range[0]), int(s_range[1])
+    L.n_lo, L.n_hi = int(n_range[0]), int(n_range[1])
+    L.m_lo, L.m_hi = int(m_range[0]), int(m_range[1])
+    L.hemispheres = int(hemispheres)
+    ns, nsp = i64(), i64()
+    st = C.c_void_p(stream) if stream else None
+    rc = _lib.fstat_lattice_grid(C.byref(L), None, None, None, 0, C.byref(ns), None, 0, C.byref(nsp), st)
+    if rc != FSTAT_OK:
+        raise FstatError(rc, "fstat_lattice_grid (count)")
+    alpha = torch.empty(ns.value, dtype=torch.float64, device="cuda")
+    delta = torch.empty(ns.value, dtype=torch.float64, device="cuda")
+    nm = torch.empty((ns.value, 3), dtype=torch.int64, device="cuda")
+    fdot = torch.empty(nsp.value, dtype=torch.float64, device="cuda")
+    rc = _lib.fstat_lattice_grid(C.byref(L), C.c_void_p(alpha.data_ptr()), C.c_void_p(delta.data_ptr()),
+                                 C.c_void_p(nm.data_ptr()), ns.value, C.byref(ns),
+                                 C.c_void_p(fdot.data_ptr()), nsp.value, C.byref(nsp), st)
+    if rc != FSTAT_OK:
+        raise FstatError(rc, "fstat_lattice_grid")
+    return alpha, delta, nm, fdot
+
+
+def lattice_grid_status(M, **kw) -> int:
+    """fstat_lattice_grid's status for arguments that may be invalid (count-only call)."""
+    L = fstat_lattice()
+    Mf = np.asarray(M, np.float64).reshape(16)
+    for i in range(16):
+        L.M[i] = float(Mf[i])
+    for k, v in kw.items():
+        setattr(L, k, v)
+    ns, nsp = i64(), i64()
+    return _lib.fstat_lattice_grid(C.byref(L), None, None, None, 0, C.byref(ns), None, 0, C.byref(nsp), None)
 
 
 def plan_create_status(desc_kwargs_bands, **kw) -> int:

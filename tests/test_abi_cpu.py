@@ -145,3 +145,23 @@ def test_both_or_neither_series_rejected(fs):
     arr[0].x32 = x32.ctypes.data_as(C.POINTER(C.c_float))
     assert fs._lib.fstat_plan_create(C.byref(h), C.byref(d)) == fs.FSTAT_ERR_ARG   # both
     del b
+
+
+def test_lattice_struct_and_argument_checks(fs):
+    """fstat_lattice_grid refuses invalid arguments on the host, before any CUDA
+    call: coupled spindown and sky rows (not a product grid), a bad hemisphere
+    count, empty ranges, non-finite entries."""
+    assert C.sizeof(fs.fstat_lattice) == 16 * 8 + 3 * 8 + 6 * 8 + 8
+    M = np.zeros((4, 4))
+    M[1, 1], M[2, 2], M[3, 3] = 1e-14, 1e3, 1e3
+    ok = dict(dt=2.0, f_ref=100.0, eps=0.4, s_lo=0, s_hi=3, n_lo=-2, n_hi=2, m_lo=-2, m_hi=2,
+              hemispheres=1)
+    for bad in ((1, 2), (1, 3), (2, 1), (3, 1)):
+        Mc = M.copy()
+        Mc[bad] = 1e-3
+        assert fs.lattice_grid_status(Mc, **ok) == fs.FSTAT_ERR_ARG, bad
+    for k, v in (("hemispheres", 3), ("dt", 0.0), ("f_ref", -1.0), ("s_hi", -1), ("n_hi", -3)):
+        assert fs.lattice_grid_status(M, **dict(ok, **{k: v})) == fs.FSTAT_ERR_ARG, k
+    Mn = M.copy()
+    Mn[2, 2] = float("nan")
+    assert fs.lattice_grid_status(Mn, **ok) == fs.FSTAT_ERR_ARG
