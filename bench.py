@@ -248,6 +248,131 @@ def source_hash():
     return h.hexdigest()[:16]
 
 
+def _timed(stream, fn, flush=None):
+    """Milliseconds of fn() on the plan's stream, CUDA events, L2 flushed first."""
+    import torch
+    if flush is not None:
+        with torch.cuda.stream(stream):
+            flush.add_(1.0)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    fn()
+    e1.record(stream)
+    e1.synchronize()
+    return e0.elapsed_time(e1)
+
+
+def run_banded(args, stream, flush, peak):
+    """The batching workload: 16 float32 bands of 1-4 sidereal days (N = 43082 ..
+    172328, N_fft 2^17 .. 2^19, sigma per band, f_off = 100 + (1 - 2^-5) b), 512 sky
+    x 16 spindowns per band, 2F > 30, one plan.  Aggregate: whole searches; per
+    band: searches of the band's cell range.  Roofline: the bands' FFT FLOP
+    (2 x 5 N log2 N per cell) over the time, against the FP32 peak."""
+    from paper_1410_3677_gb300 import fstat
+    from paper_1410_3677_gb300 import synth as S
+    w = S.workload(4)
+    plan = fstat.Plan(w.bands, w.alpha, w.delta, w.fdot, w.thr_2F, lat=w.lat, gamma=w.gamma,
+                      upsample=w.upsample, form=fstat.FP32_BATCHED, cand_capacity=1 << 26,
+                      stream=stream.cuda_stream)
+    per_band_cells = w.n_sky * w.n_spin
+    flop = [per_band_cells * 2 * 5 * b.n_fft * math.log2(b.n_fft) for b in w.bands]
+    evals = [per_band_cells * (b.n_fft // 2 - 1) for b in w.bands]
+    for _ in range(2):
+        plan.search()                        # the second search captures the graph
+    ms = [_timed(stream, plan.search, flush) for _ in range(max(2, min(args.steps, 5)))]
+    agg_ms = statistics.mean(ms)
+    bands = []
+    for bi, b in enumerate(w.bands):
+        lo, hi = bi * per_band_cells, (bi + 1) * per_band_cells
+        plan.search(lo, hi)
+        bms = min(_timed(stream, lambda: plan.search(lo, hi), flush) for _ in range(2))
+        bands.append({"band": bi, "n": int(b.n), "n_fft": int(b.n_fft), "cells": per_band_cells,
+                      "ms": round(bms, 4), "f_evals_per_s": evals[bi] / (bms / 1e3),
+                      "roofline_frac": round(flop[bi] / (bms / 1e3) / 1e12 / peak, 4)})
+    _, n_total = plan.candidates(cap=0)
+    plan.close()
+    return {"workload": w.name, "n_bands": len(w.bands), "n_cells": per_band_cells * len(w.bands),
+            "value": sum(evals) / (agg_ms / 1e3), "unit": UNIT, "ms_per_search": round(agg_ms, 3),
+            "searches": len(ms), "candidates": int(n_total),
+            "roofline": {"bound": "alu", "achieved": round(sum(flop) / (agg_ms / 1e3) / 1e12, 3),
+                         "peak": round(peak, 2), "unit": "TFLOP/s",
+                         "frac": round(sum(flop) / (agg_ms / 1e3) / 1e12 / peak, 4),
+                         "basis": "2 x 5 N log2 N FLOP per cell over the bands' transform lengths"},
+            "per_band": bands,
+            "note": "one plan over all bands; bands run one after another, each as launch pairs "
+                    "over sky batches (L2 flushed before each timed search)"}
+
+
+def run_large(args, stream, flush, peak):
+    """The large grid: one band of N = 86164, N_fft = 2^18, 65536 sky x 256 spindown
+    (16.8 M cells), 64 injections, 2F > 30, searched once as 256 resumable cell
+    ranges of 256 sky positions, each range's candidates drained to the host
+    (device sort, copy, expansion) before the next; the sustained rate includes
+    the drains.  Beside it the plain FP64 form on a 1024 x 16 subgrid."""
+    from paper_1410_3677_gb300 import fstat
+    from paper_1410_3677_gb300 import synth as S
+    import torch
+    w = S.workload(5)
+    b = w.bands[0]
+    plan = fstat.Plan(w.bands, w.alpha, w.delta, w.fdot, w.thr_2F, lat=w.lat, gamma=w.gamma,
+                      upsample=w.upsample, form=fstat.FP32_BATCHED, cand_capacity=1 << 27,
+                      stream=stream.cuda_stream)
+    cells = w.n_sky * w.n_spin
+    ranges = 256
+    step = cells // ranges
+    plan.search(0, w.n_spin)                 # warm-up on one sky position
+    out = None
+    n_cand = 0
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    dev_ms = 0.0
+    drain_s = 0.0
+    max_range = 0
+    for r in range(ranges):
+        lo, hi = r * step, cells if r == ranges - 1 else (r + 1) * step
+        dev_ms += _timed(stream, lambda: plan.search(lo, hi))
+        td = time.perf_counter()
+        _, nt = plan.candidates(cap=0)
+        if out is None or out.size < nt:
+            out = np.empty(nt + nt // 4 + 1024, fstat.CAND_DTYPE)
+        c, nt = plan.candidates(out=out)
+        drain_s += time.perf_counter() - td
+        n_cand += int(nt)
+        max_range = max(max_range, int(nt))
+    wall = time.perf_counter() - t0
+    plan.close()
+    nb = b.n_fft // 2 - 1
+    flop_cell = 2 * 5 * b.n_fft * math.log2(b.n_fft)
+    sub_sky, sub_spin = 1024, 16
+    spins = np.linspace(0, w.n_spin - 1, sub_spin).round().astype(np.int64)
+    p64 = fstat.Plan(w.bands, w.alpha[:sub_sky], w.delta[:sub_sky], w.fdot[spins], w.thr_2F,
+                     lat=w.lat, gamma=w.gamma, upsample=w.upsample, form=fstat.FP64_PLAIN,
+                     cand_capacity=1 << 24, stream=stream.cuda_stream)
+    p64.search(0, sub_spin)
+    ms64 = _timed(stream, p64.search)
+    ev64 = p64.info()["f_evals"]
+    p64.close()
+    fp64 = ev64 / (ms64 / 1e3)
+    sustained = cells * nb / wall
+    return {"workload": w.name, "n_cells": cells, "value": sustained, "unit": UNIT,
+            "wall_s": round(wall, 3), "device_s": round(dev_ms / 1e3, 3), "ranges": ranges,
+            "drain_s": round(drain_s, 3), "candidates_streamed": n_cand,
+            "max_candidates_per_range": max_range,
+            "device_rate": cells * nb / (dev_ms / 1e3),
+            "roofline": {"bound": "alu", "achieved": round(cells * flop_cell / wall / 1e12, 3),
+                         "peak": round(peak, 2), "unit": "TFLOP/s",
+                         "frac": round(cells * flop_cell / wall / 1e12 / peak, 4),
+                         "basis": "2 x 5 N log2 N FLOP per cell over the sustained wall time"},
+            "fp64_plain": {"value": fp64, "unit": UNIT, "dtype": "f64",
+                           "sample": f"{sub_sky} sky x {sub_spin} spindown subgrid (spindowns spread "
+                                     f"over the range), one cell per launch pair",
+                           "roofline_frac": round(flop_cell * ev64 / nb / (ms64 / 1e3) / 1e12 / peak, 6)},
+            "speedup_vs_fp64_plain": sustained / fp64,
+            "note": "wall time of the 256 range searches and their candidate drains to the host "
+                    "(72-byte candidates: sky, frequency, spindown, F and indices)"}
+
+
 def run_ours(args, rank, world, dist):
     import torch
     from paper_1410_3677_gb300 import fstat
@@ -472,6 +597,12 @@ def run_ours(args, rank, world, dist):
                            "the search) + fstat_search + fstat_candidates_get (device->host + sort); "
                            "the plan is created once before the timed steps"}
 
+    banded = large = None
+    if rank == 0 and world == 1 and not args.skip_banded:
+        banded = run_banded(args, stream, flush, peak)
+    if rank == 0 and world == 1 and not args.skip_large:
+        large = run_large(args, stream, flush, peak)
+
     cpu = None
     if rank == 0 and world == 1 and not args.skip_cpu:
         cpu = oracle_rate(w)
@@ -491,7 +622,8 @@ def run_ours(args, rank, world, dist):
             "candidates": int(n_total), "gpu_launches": int(launches),
             "roofline": roofline, "fp64_plain": fp64, "interbin": interbin,
             "speedup_vs_fp64_plain": (value / world / fp64["value"]) if fp64 else None,
-            "e2e": e2e, "cpu_baseline": cpu, "clocks": clk}
+            "e2e": e2e, "cpu_baseline": cpu, "clocks": clk,
+            "banded_16_bands": banded, "large_65536x256": large}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -507,6 +639,8 @@ def main():
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-interbin", action="store_true")
+    ap.add_argument("--skip-banded", action="store_true", help="no 16-band batching workload leg")
+    ap.add_argument("--skip-large", action="store_true", help="no 65536 x 256 large-grid leg")
     ap.add_argument("--n-sky", type=int, default=0, help="first n sky positions only (profiling)")
     ap.add_argument("--cand-capacity", type=int, default=1 << 27)
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shapes")
