@@ -224,7 +224,9 @@ fstat_status fstat_plan_kernel_stats(const fstat_plan *plan, fstat_kernel_stat *
    CUDA events, changing one choice at a time -- FFT engine (two-stage radix
    32x16 / radix-8 Stockham), pass-2 tile (128 or 256 threads) and loader (bulk
    copies or per-thread loads with L2 prefetch), cells per launch pair, one fused
-   ticket-ordered launch or two launches -- keeps a change only when it is at
+   ticket-ordered launch or two launches, and at N_fft = 2^18 the passes in
+   paired FP32 instructions (two values per instruction: none, pass 2 only, or
+   both passes) -- keeps a change only when it is at
    least 1 % faster, and leaves the plan configured with the best found.  The
    candidates of the tuning searches are discarded (fstat_candidates_get then
    reports none until the next fstat_search).  *chosen (may be NULL) receives the
@@ -232,7 +234,9 @@ fstat_status fstat_plan_kernel_stats(const fstat_plan *plan, fstat_kernel_stat *
    depend on the choice beyond FP32 rounding (every shape computes the same
    transforms).  FSTAT_ERR_ARG for an FP64_PLAIN plan or sample_cells < 1. */
 typedef struct {
-    int32_t engine;          /* 2: two-stage engine, 1: radix-8 engine */
+    int32_t engine;          /* 2: two-stage engine, 1: radix-8 engine; 3: two-stage with
+                                pass 2 in paired FP32 instructions at N_fft = 2^18, 4: with
+                                both passes paired */
     int32_t pass2_threads;   /* 128 or 256 */
     int32_t pass2_bulk_copy; /* 1: bulk-copy staging, 0: per-thread loads */
     int32_t fused;           /* 1: one ticket-ordered launch per batch */

@@ -189,15 +189,32 @@ void stage1_twiddles(int logm, std::vector<double> &o) {
         }
 }
 
+// Stage-1 twiddles of a 512-point pass (radix 32 then 16) as packed pairs of
+// jobs (2k, 2k + 1): [r][k] = (cos a_2k, cos a_2k+1, -sin a_2k, -sin a_2k+1),
+// a_j = 2 pi (r j mod 512) / 512, r < 16, k < 16.
+void packed512_twiddles(std::vector<double> &o) {
+    o.assign(16 * 16 * 4, 0.0);
+    for (int r = 0; r < 16; ++r)
+        for (int k = 0; k < 16; ++k)
+            for (int e = 0; e < 2; ++e) {
+                const double a = kTwoPi * (double)((r * (2 * k + e)) % 512) / 512.0;
+                o[(size_t)(4 * (r * 16 + k) + e)] = cos(a);
+                o[(size_t)(4 * (r * 16 + k) + 2 + e)] = -sin(a);
+            }
+}
+
 void build_twiddles(Plan &p, const std::vector<int> &logs, int &n_alloc) {
     std::vector<double> hd;
     std::vector<size_t> offs;
+    constexpr int kSets = 7;
     for (int lg : logs) {
-        std::vector<double> a, b, c, d, e, f;
+        std::vector<double> a, b, c, d, e, f, g;
         host_twiddles(lg, a, b, c, d);
         stage1_twiddles(log_n1(lg), e);
         stage1_twiddles(log_n2(lg), f);
-        for (auto *v : {&a, &b, &c, &d, &e, &f}) {
+        if (lg == 18) packed512_twiddles(g);
+        for (auto *v : {&a, &b, &c, &d, &e, &f, &g}) {
+            while (hd.size() % 4) hd.push_back(0.0);   // 16-byte aligned float tables
             offs.push_back(hd.size());
             hd.insert(hd.end(), v->begin(), v->end());
         }
@@ -209,12 +226,14 @@ void build_twiddles(Plan &p, const std::vector<int> &logs, int &n_alloc) {
     check(cudaMemcpy(df, hf.data(), hf.size() * sizeof(float), cudaMemcpyHostToDevice), "twiddles");
     for (size_t i = 0; i < logs.size(); ++i) {
         TwiddleSet t;
+        const size_t *o = &offs[kSets * i];
         t.logn = logs[i];
-        t.in1_d = dd + offs[6 * i]; t.in2_d = dd + offs[6 * i + 1];
-        t.lo_d = dd + offs[6 * i + 2]; t.hi_d = dd + offs[6 * i + 3];
-        t.in1_f = df + offs[6 * i]; t.in2_f = df + offs[6 * i + 1];
-        t.lo_f = df + offs[6 * i + 2]; t.hi_f = df + offs[6 * i + 3];
-        t.s1_f = df + offs[6 * i + 4]; t.s2_f = df + offs[6 * i + 5];
+        t.in1_d = dd + o[0]; t.in2_d = dd + o[1];
+        t.lo_d = dd + o[2]; t.hi_d = dd + o[3];
+        t.in1_f = df + o[0]; t.in2_f = df + o[1];
+        t.lo_f = df + o[2]; t.hi_f = df + o[3];
+        t.s1_f = df + o[4]; t.s2_f = df + o[5];
+        if (logs[i] == 18) t.p512_f = reinterpret_cast<const float4 *>(df + o[6]);
         p.tw.push_back(t);
     }
 }
@@ -381,6 +400,7 @@ void create_impl(Plan &p, const fstat_plan_desc *d) {
         }
         if (const char *v = getenv("FSTAT_PF_DIST")) p.pf_dist = std::max(0, atoi(v));
         if (const char *v = getenv("FSTAT_TMA")) p.tma = atoi(v) != 0;
+        if (const char *v = getenv("FSTAT_PACKED")) p.packed = std::max(0, std::min(2, atoi(v)));
         if (const char *v = getenv("FSTAT_P2_THREADS")) p.p2_threads = atoi(v) == 128 ? 128 : 256;
         if (const char *v = getenv("FSTAT_FUSED_SLOTS")) p.fused_slots = std::max(2, std::min(256, atoi(v)));
         if (const char *v = getenv("FSTAT_FUSED_AHEAD")) p.fused_ahead = std::max(1, atoi(v));
@@ -1180,6 +1200,11 @@ fstat_status fstat_plan_autotune(fstat_plan *p, int64_t sample_cells, fstat_tuni
           try_set([&] { p->fused = !old; }, [&] { p->fused = old; }); }
         { const int old = p->engine;
           try_set([&] { p->engine = old == 2 ? 1 : 2; }, [&] { p->engine = old; }); }
+        for (int pkv : {0, 2}) {   // paired arithmetic in neither pass, or in both
+            const int old = p->packed;
+            if (pkv == old) continue;
+            try_set([&] { p->packed = pkv; }, [&] { p->packed = old; });
+        }
         p->ev_pool.push_back(e0);
         p->ev_pool.push_back(e1);
         p->timing_every = timing;
@@ -1188,7 +1213,7 @@ fstat_status fstat_plan_autotune(fstat_plan *p, int64_t sample_cells, fstat_tuni
         p->searched = false;
         p->prev_begin = p->prev_end = -1;
         if (chosen) {
-            chosen->engine = p->engine;
+            chosen->engine = p->engine == 2 && p->packed ? 2 + p->packed : p->engine;
             chosen->pass2_threads = p->p2_threads;
             chosen->pass2_bulk_copy = p->tma ? 1 : 0;
             chosen->fused = p->fused ? 1 : 0;

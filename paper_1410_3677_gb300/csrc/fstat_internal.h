@@ -34,6 +34,9 @@ struct TwiddleSet {
     // second engine: stage-1 twiddles W_M^{r j} laid out [r][j], r < R1, j < R0
     // (float), for the rows (M = N1 = R0 R1, pass 2) and the columns (M = N2, pass 1)
     const float *s1_f = nullptr, *s2_f = nullptr;
+    // packed passes (N_fft = 2^18): stage-1 twiddles of a 512-point pass as pairs,
+    // [r][k] = (cos a_2k, cos a_2k+1, -sin a_2k, -sin a_2k+1), a_j = 2 pi r j / 512
+    const float4 *p512_f = nullptr;
 };
 
 // Per-sky normaliser record: na, nb, nab, 0 in FP64 (doubles 0..3), then the
@@ -128,6 +131,8 @@ struct Plan {
     uint32_t *fctl = nullptr;      // per worker: 1 + 2 * cell_batch counters of the fused launch
     size_t slot_cells = 0;         // cells of scratch per worker (>= cell_batch, >= the fused ring)
     int fused_slots = kFusedSlots, fused_ahead = kFusedAhead;
+    int packed = 1;                // N_fft = 2^18 in paired FP32 arithmetic (passes3.cuh): 0 neither
+                                   // pass, 1 pass 2, 2 both passes
     int fused_tpi = 1;             // tiles per ticket of the fused launch (power of two)
     int64_t fused_batch = 1;       // cells per fused launch (a sky batch)
     int64_t pf_dist = 0;           // two-stage pass 2: L2 prefetch distance in CTAs (0: off)

@@ -1,0 +1,272 @@
+// The FP32 search passes in packed arithmetic (packed.cuh) for transforms whose
+// two passes have length 512 (N_fft = 2^18: N1 = N2 = 512), the length of the
+// two-sidereal-day segments.  Same four-step split, scratch layout, tiles and
+// launch shapes as the second engine's passes (passes2.cuh); what changes is how
+// a thread's 32 elements are transformed:
+//
+//  - the radix-32 first stage of a pass is split by one decimation-in-frequency
+//    step into two 16-point DFTs, a_m = x_m + x_{m+16} and
+//    b_m = (x_m - x_{m+16}) W_32^m, which run as one packed 16-point DFT; its
+//    outputs come out as the pairs (X_{2k}, X_{2k+1}) of adjacent outputs;
+//  - those pairs are exactly the two stage-1 jobs (2k, 2k + 1) a thread takes
+//    next, so the exchange holds them side by side, (Re X_{2k}, Re X_{2k+1},
+//    Im X_{2k}, Im X_{2k+1}) in one 16-byte word, and the radix-16 second stage,
+//    its twiddles and the F epilogue run packed as well;
+//  - in pass 2 the four-step twiddle W_N^{k1 l2} of inputs m and m + 16 folds
+//    into the split: with T_m = W_N^{l2 (j + 16 m)} and c = W_N^{256 l2},
+//    a_m = T_m (s_m + c s_{m+16}) and b_m = T_m W_32^m (s_m - c s_{m+16}); the pair
+//    (T_m, T_m W_32^m) advances by the packed factor (W_N^{16 l2}, W_N^{16 l2} W_32).
+#pragma once
+
+#include "packed.cuh"
+#include "passes2.cuh"
+
+namespace fstat {
+namespace p3 {
+
+using pk::PC;
+
+constexpr int kM = 512;          // pass length (both passes at N_fft = 2^18)
+constexpr int kR0 = 32, kR1 = 16;
+// Pass-2 exchange: per sequence 16 stage-1 job pairs x 16 elements, 16-byte
+// words, rows of 17 words so that the 8 lanes of a quarter-warp reading the same
+// element of consecutive job pairs fall in 8 different bank groups.
+constexpr int kRowW = 17;
+constexpr int kSeqW = 16 * kRowW;   // 16-byte words per sequence
+
+// Stage-1 twiddles of a 512-point pass as packed pairs: entry [r][k] =
+// (cos a_{2k}, cos a_{2k+1}, -sin a_{2k}, -sin a_{2k+1}), a_j = 2 pi r j / 512,
+// r < 16, k < 16 (built on the host, 4 KiB).
+__device__ __forceinline__ PC tw1(const float4 *__restrict__ t, int r, int k) {
+    const float4 v = __ldg(t + r * 16 + k);
+    return {make_float2(v.x, v.y), make_float2(v.z, v.w)};
+}
+
+// e^{-2 pi i m / 32} on one scalar complex value
+__device__ __forceinline__ void w32_scalar(int m, float &xr, float &xi) { eng2::mul_w32<-1>(m, xr, xi); }
+
+// --------------------------------------------------------------------- pass 1
+// Columns k1 of the demodulated series: SearchLoad2 gives the stage-0 inputs
+// (12 of 32 non-zero: the upper five eighths of each column lie in the zero
+// padding when n <= 3 N_fft / 8), ScratchStore2 writes the transposed outputs.
+// 256 threads: 8 columns x 2 transforms, 16 threads per sequence; CTA-wide
+// exchange in the 16-byte layout of the second engine (element i at i + 2 (i/32)).
+template <int LOGN, int Z1>
+__global__ void __launch_bounds__(256, 3)
+k_pass1p(SearchLoad2<Cfg2<LOGN, 1>> ld, ScratchStore2<Cfg2<LOGN, 1>> st, const float4 *__restrict__ tws) {
+    using C = Cfg2<LOGN, 1>;
+    static_assert(C::M == kM && C::SEQ == 16 && C::THREADS == 256, "512-point columns, 16 sequences");
+    static_assert(Z1 == 3 || Z1 == 4, "known-zero eighths of a column");
+    constexpr int SEQ = C::SEQ;
+    constexpr int RL = eng2::row_ld16(kM);
+    constexpr int NZ = kR0 * Z1 / 8;   // stage-0 inputs that can be non-zero (12 or 16)
+    ld.init(blockIdx.x, blockIdx.y, blockIdx.y);
+    st.init(blockIdx.x, blockIdx.y, blockIdx.y);
+    float2 *sd = reinterpret_cast<float2 *>(eng2::dyn_smem());
+    const int s = (int)threadIdx.x % SEQ;   // sequence: column f = s / 2, transform t = s & 1
+    const int j = (int)threadIdx.x / SEQ;   // stage-0 butterfly; stage-1 job pair (2j, 2j + 1)
+    eng2::Job q{s, s & 1, s >> 1, j};
+
+    // stage 0: elements j + 16 r of the column, r < NZ non-zero
+    PC P[16];
+    {
+        float re[NZ], im[NZ];
+        ld.template load<NZ, 16>(q, re, im);
+#pragma unroll
+        for (int m = 0; m < 16; ++m) {
+            // a_m = x_m + x_{m+16}, b_m = (x_m - x_{m+16}) W_32^m; x_{m+16} is zero (m + 16 >= NZ)
+            static_assert(NZ <= 16, "the upper half of the first stage lies in the zero padding");
+            if (m < NZ) {
+                float br = re[m], bi = im[m];
+                w32_scalar(m, br, bi);
+                P[m] = {make_float2(re[m], br), make_float2(im[m], bi)};
+            }
+        }
+    }
+    pk::dft16<NZ>(P);   // P[k] = (X_{2k}, X_{2k+1})
+    {
+        float4 *p4 = reinterpret_cast<float4 *>(sd + s * RL + eng2::pad16(j * kR0));
+#pragma unroll
+        for (int k = 0; k < 16; ++k) p4[k] = make_float4(P[k].re.x, P[k].re.y, P[k].im.x, P[k].im.y);
+    }
+    __syncthreads();
+    // stage 1: jobs (2j, 2j + 1), element r at (2j) + 32 r
+    PC Q[16];
+    {
+        const float4 *p4 = reinterpret_cast<const float4 *>(sd + s * RL + 2 * j);
+#pragma unroll
+        for (int r = 0; r < 16; ++r) {
+            const float4 v = p4[eng2::pad16(r * kR0) / 2];
+            Q[r] = {make_float2(v.x, v.y), make_float2(v.z, v.w)};
+        }
+    }
+#pragma unroll
+    for (int r = 1; r < 16; ++r) Q[r] = pk::cmul(Q[r], tw1(tws, r, j));
+    pk::dft16<16>(Q);
+    // outputs l2 = job + 32 p of the two jobs, one transposed store each
+    float re0[16], im0[16], re1[16], im1[16];
+#pragma unroll
+    for (int p = 0; p < 16; ++p) {
+        re0[p] = Q[p].re.x; im0[p] = Q[p].im.x;
+        re1[p] = Q[p].re.y; im1[p] = Q[p].im.y;
+    }
+    eng2::Job q0{s, s & 1, s >> 1, 2 * j}, q1{s, s & 1, s >> 1, 2 * j + 1};
+    st.template store<16, kR0>(q0, re0, im0);
+    st.template store<16, kR0>(q1, re1, im1);
+}
+
+// --------------------------------------------------------------------- pass 2
+// Dynamic shared memory of the packed pass 2 before its mbarrier (8 bytes after
+// it): the exchange of 8 sequences, which also receives the staged tile.
+template <class C>
+__host__ __device__ constexpr size_t pass2p_smem() {
+    return (size_t)C::SEQ * kSeqW * 16;
+}
+
+// Rows l2 of the scratch, staged by a bulk copy (ScratchLoadTMA's copy and
+// bounded wait), four-step twiddle folded into the split, packed row DFTs, then
+// F, threshold and compaction.  128 threads: 4 rows x 2 transforms, a warp per
+// row (F_a in lanes 0-15, F_b in lanes 16-31).
+// F per bin of the packed outputs (the epilogue of SearchEpi2 on pairs of jobs).
+// Lanes l (F_a) and l ^ 16 (F_b) hold the same bins; the a lane evaluates F on
+// the outputs p < H, the b lane on p >= H, each taking the partner's values for
+// its half with one shuffle per value.
+template <class C, bool LOWER>
+__device__ __forceinline__ void epilogue(const SearchEpi2<C, LOWER> &ep, int t, int jp, int l2, const PC *Y) {
+    constexpr int NP = LOWER ? 8 : 16;   // outputs p of each job used
+    constexpr int H = NP / 2;
+    const int lane = (int)threadIdx.x & 31;
+    const bool full = ep.nab != 0.f;
+    float2 Fv[H];
+#pragma unroll
+    for (int u = 0; u < H; ++u) {
+        // values are selected, never indexed by the lane's transform (that would
+        // move Y to local memory)
+        const PC lo = Y[u], hi = Y[u + H];
+        if (full) {
+            const PC send = t == 0 ? hi : lo, mine = t == 0 ? lo : hi;
+            PC oth;
+            oth.re.x = __shfl_xor_sync(0xffffffffu, send.re.x, 16);
+            oth.re.y = __shfl_xor_sync(0xffffffffu, send.re.y, 16);
+            oth.im.x = __shfl_xor_sync(0xffffffffu, send.im.x, 16);
+            oth.im.y = __shfl_xor_sync(0xffffffffu, send.im.y, 16);
+            const PC a = t == 0 ? mine : oth, b = t == 0 ? oth : mine;
+            const float2 pa = pk::pfma(a.re, a.re, pk::pmul(a.im, a.im));
+            const float2 pb = pk::pfma(b.re, b.re, pk::pmul(b.im, b.im));
+            const float2 cr = pk::pfma(a.re, b.re, pk::pmul(a.im, b.im));
+            Fv[u] = pk::pfma(pa, pk::bc(ep.na), pk::pfma(pb, pk::bc(ep.nb), pk::pmul(cr, pk::bc(ep.nab))));
+        } else {
+            const float2 plo = pk::pfma(lo.re, lo.re, pk::pmul(lo.im, lo.im));
+            const float2 phi = pk::pfma(hi.re, hi.re, pk::pmul(hi.im, hi.im));
+            const float2 ps = t == 0 ? phi : plo, pm = t == 0 ? plo : phi;
+            float2 po;
+            po.x = __shfl_xor_sync(0xffffffffu, ps.x, 16);
+            po.y = __shfl_xor_sync(0xffffffffu, ps.y, 16);
+            const float2 pa = t == 0 ? pm : po, pb = t == 0 ? po : pm;
+            Fv[u] = pk::pfma(pa, pk::bc(ep.na), pk::pmul(pb, pk::bc(ep.nb)));
+        }
+    }
+    // bins: job jj = 2 jp + e, output p = u + t H: l1 = jj + 32 p, bin = N2 l1 + l2 (< 2^19)
+    const int lo = (int)ep.bin_lo;
+    const unsigned span = (unsigned)(ep.bin_hi - ep.bin_lo);
+    const int bin0 = C::N2 * (2 * jp + kR0 * t * H) + l2;
+    bool pr[2 * H];
+    bool any = false;
+#pragma unroll
+    for (int u = 0; u < H; ++u)
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+            const int bin = bin0 + C::N2 * (e + kR0 * u);
+            const float f = e ? Fv[u].y : Fv[u].x;
+            pr[2 * u + e] = ((unsigned)(bin - lo) <= span) && (f > ep.thr_half);
+            any |= pr[2 * u + e];
+        }
+    if (!__any_sync(0xffffffffu, any)) return;
+#pragma unroll
+    for (int u = 0; u < H; ++u)
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+            const bool hit = pr[2 * u + e];
+            const unsigned m = __ballot_sync(0xffffffffu, hit);
+            if (m) {
+                const int leader = __ffs(m) - 1;
+                unsigned long long b0 = 0;
+                if (lane == leader) b0 = atomicAdd(ep.count, (unsigned long long)__popc(m));
+                b0 = __shfl_sync(0xffffffffu, b0, leader);
+                if (hit) {
+                    const unsigned long long idx = b0 + __popc(m & ((1u << lane) - 1u));
+                    const float f = e ? Fv[u].y : Fv[u].x;
+                    if (idx < ep.cap)
+                        ep.out[idx] = CandRecord{ep.cell, (uint32_t)(bin0 + C::N2 * (e + kR0 * u)), (double)f};
+                }
+            }
+        }
+}
+
+template <int LOGN, bool LOWER>
+__global__ void __launch_bounds__(128, 6)
+k_pass2p(ScratchLoadTMA<Cfg2<LOGN, 2, 128>> ld, SearchEpi2<Cfg2<LOGN, 2, 128>, LOWER> ep,
+         const float4 *__restrict__ tws) {
+    using C = Cfg2<LOGN, 2, 128>;
+    static_assert(C::M == kM && C::SEQ == 8 && C::F == 4 && C::TPF == 16, "512-point rows, 4-row tiles");
+    static_assert(2 * C::F * C::N1 * sizeof(float2) <= pass2p_smem<C>(), "the staged tile fits the exchange area");
+    ld.prefetch_ahead();
+    ld.init(blockIdx.x, blockIdx.y, blockIdx.y);
+    ld.bar = reinterpret_cast<uint64_t *>(eng2::dyn_smem() + pass2p_smem<C>());   // after this exchange
+    ep.init(blockIdx.x, blockIdx.y, blockIdx.y);
+    ld.stage();
+    const int w = (int)threadIdx.x >> 5, lane = (int)threadIdx.x & 31;
+    const int t = lane >> 4;           // transform
+    const int j = lane & 15;           // stage-0 butterfly; stage-1 job pair (2j, 2j + 1)
+    const int f = w;                   // tile row
+    const int l2 = ld.l2_0 + f;
+    // four-step factors: T_0 = W^{l2 j}, step W^{16 l2}, c = W^{256 l2}
+    const float2 w0 = ld.tw.wn(l2 * j), stp = ld.tw.wn(16 * l2), cc = ld.tw.wn(256 * l2);
+    // (T_m, T_m W_32^m) advance by (stp, stp W_32)
+    PC T = {make_float2(w0.x, w0.x), make_float2(w0.y, w0.y)};
+    float s1r = stp.x, s1i = stp.y;
+    w32_scalar(1, s1r, s1i);
+    const PC S = {make_float2(stp.x, s1r), make_float2(stp.y, s1i)};
+    // wait for the tile's bulk copy (bounded, as ScratchLoadTMA::load)
+    if (!ptx::mbar_try_wait(ld.bar, 0)) {
+        const uint64_t t0 = ptx::globaltimer_ns();
+        bool late = false;
+        while (!ptx::mbar_try_wait(ld.bar, 0)) {
+            const uint64_t dt = ptx::globaltimer_ns() - t0;
+            if (!late && dt > 1000000000ull) { atomicExch(ld.err, 1u); late = true; }
+            if (dt > 2000000000ull) break;   // reported above; results are discarded
+        }
+    }
+    PC P[16];
+    {
+        const float2 *row = ld.rows + 2 * (f * C::N1 + j) + t;   // element k1 at row[2 k1]
+#pragma unroll
+        for (int m = 0; m < 16; ++m) {
+            const float2 lo = row[2 * 16 * m], hi = row[2 * 16 * (m + 16)];
+            // u = c s_{m+16}; A = s_m + u, D = s_m - u
+            const float ur = hi.x * cc.x - hi.y * cc.y, ui = hi.x * cc.y + hi.y * cc.x;
+            const PC X = {make_float2(lo.x + ur, lo.x - ur), make_float2(lo.y + ui, lo.y - ui)};
+            P[m] = pk::cmul(X, T);
+            if (m + 1 < 16) T = pk::cmul(T, S);
+        }
+    }
+    pk::dft16<16>(P);   // P[k] = (X_{2k}, X_{2k+1}) of row l2
+    __syncthreads();    // every warp has read its staged rows: the exchange may be overwritten
+    float4 *ex = reinterpret_cast<float4 *>(eng2::dyn_smem()) + (t * C::F + f) * kSeqW;
+#pragma unroll
+    for (int k = 0; k < 16; ++k) ex[k * kRowW + j] = make_float4(P[k].re.x, P[k].re.y, P[k].im.x, P[k].im.y);
+    __syncwarp();
+    PC Q[16];
+#pragma unroll
+    for (int r = 0; r < 16; ++r) {
+        const float4 v = ex[j * kRowW + r];
+        Q[r] = {make_float2(v.x, v.y), make_float2(v.z, v.w)};
+    }
+#pragma unroll
+    for (int r = 1; r < 16; ++r) Q[r] = pk::cmul(Q[r], tw1(tws, r, j));
+    pk::dft16<16, LOWER>(Q);
+    epilogue<C, LOWER>(ep, t, j, l2, Q);
+}
+
+}  // namespace p3
+}  // namespace fstat

@@ -5,6 +5,7 @@
 #include <algorithm>
 
 #include "passes2.cuh"
+#include "passes3.cuh"
 #include "search_launch.cuh"
 
 namespace fstat {
@@ -46,10 +47,22 @@ int launch_two(const Plan &p, int band_idx, const BandDev &b, int64_t s0, int64_
                const TwiddleSet *tw) {
     using C1 = Cfg2<LOGN, 1>;
     using C2 = Cfg2<LOGN, 2>;
+    // N_fft = 2^18: pass 2 (and, with packed = 2, pass 1) in paired FP32 arithmetic
+    const bool pk2 = LOGN == 18 && p.packed >= 1 && p.tma && p.p2_threads == 128 && tw->p512_f;
+    const bool pk1 = pk2 && p.packed >= 2;
+    if constexpr (LOGN == 18) {
+        if (pk1) {
+            const bool z3 = 8 * b.n <= 3 * (int64_t)C1::N;
+            auto k1 = z3 ? p3::k_pass1p<LOGN, 3> : p3::k_pass1p<LOGN, 4>;
+            static bool attr1p[2] = {false, false};
+            if (!attr1p[z3]) { set_smem(k1, C1::SMEM); attr1p[z3] = true; }
+            k1<<<dim3(C1::TILES, (unsigned)nc), C1::THREADS, C1::SMEM, s>>>(ld1, st1, tw->p512_f);
+        }
+    }
     // columns known zero beyond 3/8 of their length (radix-32 first stage) or 1/2
-    bool launched = false;
+    bool launched = pk1;
     if constexpr (eng2::radix0(C1::M) == 32) {
-        if (8 * b.n <= 3 * (int64_t)C1::N) {
+        if (!launched && 8 * b.n <= 3 * (int64_t)C1::N) {
             auto k1 = k_pass2<LOGN, 1, eng2::kMapFJ, SearchLoad2<C1>, ScratchStore2<C1>, 256, 3>;
             static bool attr3 = false;
             if (!attr3) { set_smem(k1, C1::SMEM); attr3 = true; }
@@ -64,6 +77,23 @@ int launch_two(const Plan &p, int band_idx, const BandDev &b, int64_t s0, int64_
         k1<<<dim3(C1::TILES, (unsigned)nc), C1::THREADS, C1::SMEM, s>>>(ld1, st1, tw->s2_f);
     }
     if (mid) record_timing_event(mid, s);
+    if constexpr (LOGN == 18) {
+        if (pk2) {
+            using D2 = Cfg2<LOGN, 2, 128>;
+            ScratchLoadTMA<D2> lt{};
+            lt.scratch = ld2.scratch;
+            lt.tw = ld2.tw;
+            lt.pf_dist = 2 * ld2.pf_dist;
+            lt.err = p.qerr;
+            const auto ep = make_epi<LOGN, LOWER, 128>(p, band_idx, b, c0, s0, cb);
+            auto k2 = p3::k_pass2p<LOGN, LOWER>;
+            constexpr size_t smem2 = p3::pass2p_smem<D2>() + 16;   // exchange + mbarrier
+            static bool attr2p = false;
+            if (!attr2p) { set_smem(k2, smem2); attr2p = true; }
+            k2<<<dim3(D2::TILES, (unsigned)nc), D2::THREADS, smem2, s>>>(lt, ep, tw->p512_f);
+            return 2;
+        }
+    }
     if (p.tma && p.p2_threads == 128) {   // smaller tiles, six CTAs per SM
         ScratchLoadTMA<Cfg2<LOGN, 2, 128>> lt{};
         lt.scratch = ld2.scratch;

@@ -42,9 +42,12 @@ def _run(fs, w, thr, env=None, **kw):
 
 
 R8 = {"FSTAT_PERSISTENT": "0", "FSTAT_ENGINE": "1"}     # radix-8 engine, two launches per batch
-TWO = {"FSTAT_PERSISTENT": "0", "FSTAT_FUSED": "0"}      # two-stage engine, two launches per batch
-DEFAULT = {"FSTAT_PERSISTENT": "0"}                       # the default (the same)
+# two-stage engine, two launches per batch, scalar FP32 (the fused launch's arithmetic)
+TWO = {"FSTAT_PERSISTENT": "0", "FSTAT_FUSED": "0", "FSTAT_PACKED": "0"}
+DEFAULT = {"FSTAT_PERSISTENT": "0"}                       # the default (pass 2 paired at 2^18)
 FUSED = {"FSTAT_PERSISTENT": "0", "FSTAT_FUSED": "1"}    # two-stage engine, one ticket-ordered launch
+PK1 = {"FSTAT_PERSISTENT": "0", "FSTAT_FUSED": "0", "FSTAT_PACKED": "1"}   # pass 2 paired at 2^18
+PK2 = {"FSTAT_PERSISTENT": "0", "FSTAT_FUSED": "0", "FSTAT_PACKED": "2"}   # both passes paired
 
 
 @pytest.mark.parametrize("base,env", [
@@ -53,14 +56,16 @@ FUSED = {"FSTAT_PERSISTENT": "0", "FSTAT_FUSED": "1"}    # two-stage engine, one
     (R8, {"FSTAT_PERSISTENT": "1", "FSTAT_PERSIST_BATCH": "5", "FSTAT_PERSIST_SLOTS": "8"}),
     (R8, {"FSTAT_ENGINE": "1", "FSTAT_ELEMS_PER_THREAD": "8"}),
     (R8, {"FSTAT_ENGINE": "1", "FSTAT_ELEMS_PER_THREAD": "8", "FSTAT_CELL_BATCH": "7", "FSTAT_STREAMS": "2"}),
-    (TWO, {"FSTAT_FUSED": "0", "FSTAT_CELL_BATCH": "7", "FSTAT_STREAMS": "2"}),
-    (TWO, {"FSTAT_FUSED": "0", "FSTAT_CELL_BATCH": "1", "FSTAT_STREAMS": "3"}),
-    (TWO, DEFAULT),
-    (TWO, {"FSTAT_CELL_BATCH": "2"}),
+    (TWO, {"FSTAT_FUSED": "0", "FSTAT_PACKED": "0", "FSTAT_CELL_BATCH": "7", "FSTAT_STREAMS": "2"}),
+    (TWO, {"FSTAT_FUSED": "0", "FSTAT_PACKED": "0", "FSTAT_CELL_BATCH": "1", "FSTAT_STREAMS": "3"}),
+    (PK1, DEFAULT),
+    (PK1, {"FSTAT_CELL_BATCH": "2"}),
+    (PK1, {"FSTAT_CELL_BATCH": "7", "FSTAT_STREAMS": "2"}),
+    (PK1, {"FSTAT_PF_DIST": "0", "FSTAT_CELL_BATCH": "9"}),
+    (PK2, {"FSTAT_PACKED": "2", "FSTAT_CELL_BATCH": "5", "FSTAT_STREAMS": "2"}),
     (TWO, {"FSTAT_TMA": "0"}),
     (TWO, {"FSTAT_P2_THREADS": "256"}),
-    (TWO, {"FSTAT_PF_DIST": "0", "FSTAT_CELL_BATCH": "9"}),
-    (TWO, {"FSTAT_CELL_BATCH": "5", "FSTAT_STREAMS": "2"}),
+    (TWO, {"FSTAT_PACKED": "0", "FSTAT_CELL_BATCH": "5", "FSTAT_STREAMS": "2"}),
     (TWO, FUSED),
     (TWO, {"FSTAT_FUSED": "1", "FSTAT_FUSED_BATCH": "3"}),
     (TWO, {"FSTAT_FUSED": "1", "FSTAT_FUSED_BATCH": "11", "FSTAT_STREAMS": "2"}),
@@ -203,13 +208,14 @@ def test_autotune_keeps_results(fs):
     p0.close()
     p = plan()
     t = p.autotune(64)
-    assert t["engine"] in (1, 2) and t["pass2_threads"] in (128, 256)
+    assert t["engine"] in (1, 2, 3, 4) and t["pass2_threads"] in (128, 256)
     assert t["cells_per_launch"] >= 1 and t["ms_per_cell"] > 0
     assert p.candidates()[1] == 0                      # tuning searches are discarded
     p.search()
     c, _ = p.candidates()
     p.close()
-    if t["engine"] == 2:
+    default = t["engine"] == 3 and t["pass2_threads"] == 128 and t["pass2_bulk_copy"] == 1 and t["fused"] == 0
+    if default:                      # the default kernels: bit for bit
         assert np.array_equal(c, ref)
     else:
         keys = ("sky", "spin", "bin")
