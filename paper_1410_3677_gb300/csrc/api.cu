@@ -400,7 +400,7 @@ void create_impl(Plan &p, const fstat_plan_desc *d) {
         }
         if (const char *v = getenv("FSTAT_PF_DIST")) p.pf_dist = std::max(0, atoi(v));
         if (const char *v = getenv("FSTAT_TMA")) p.tma = atoi(v) != 0;
-        if (const char *v = getenv("FSTAT_PACKED")) p.packed = std::max(0, std::min(2, atoi(v)));
+        if (const char *v = getenv("FSTAT_PACKED")) p.packed = std::max(0, std::min(3, atoi(v)));
         if (const char *v = getenv("FSTAT_P2_THREADS")) p.p2_threads = atoi(v) == 128 ? 128 : 256;
         if (const char *v = getenv("FSTAT_FUSED_SLOTS")) p.fused_slots = std::max(2, std::min(256, atoi(v)));
         if (const char *v = getenv("FSTAT_FUSED_AHEAD")) p.fused_ahead = std::max(1, atoi(v));

@@ -132,7 +132,8 @@ struct Plan {
     size_t slot_cells = 0;         // cells of scratch per worker (>= cell_batch, >= the fused ring)
     int fused_slots = kFusedSlots, fused_ahead = kFusedAhead;
     int packed = 1;                // N_fft = 2^18 in paired FP32 arithmetic (passes3.cuh): 0 neither
-                                   // pass, 1 pass 2, 2 both passes
+                                   // pass, 1 pass 2, 2 both passes, 3 pass 2 and the second
+                                   // stage of pass 1
     int fused_tpi = 1;             // tiles per ticket of the fused launch (power of two)
     int64_t fused_batch = 1;       // cells per fused launch (a sky batch)
     int64_t pf_dist = 0;           // two-stage pass 2: L2 prefetch distance in CTAs (0: off)

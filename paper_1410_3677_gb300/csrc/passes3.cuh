@@ -115,6 +115,56 @@ k_pass1p(SearchLoad2<Cfg2<LOGN, 1>> ld, ScratchStore2<Cfg2<LOGN, 1>> st, const f
     st.template store<16, kR0>(q1, re1, im1);
 }
 
+// The same columns with a scalar first stage (the second engine's half-zero
+// radix-32 DFT, outputs stored in the packed exchange layout) and the packed
+// second stage.
+template <int LOGN, int Z1>
+__global__ void __launch_bounds__(256, 3)
+k_pass1h(SearchLoad2<Cfg2<LOGN, 1>> ld, ScratchStore2<Cfg2<LOGN, 1>> st, const float4 *__restrict__ tws) {
+    using C = Cfg2<LOGN, 1>;
+    static_assert(C::M == kM && C::SEQ == 16 && C::THREADS == 256, "512-point columns, 16 sequences");
+    static_assert(Z1 == 3 || Z1 == 4, "known-zero eighths of a column");
+    constexpr int SEQ = C::SEQ;
+    constexpr int RL = eng2::row_ld16(kM);
+    constexpr int NZ = kR0 * Z1 / 8;
+    ld.init(blockIdx.x, blockIdx.y, blockIdx.y);
+    st.init(blockIdx.x, blockIdx.y, blockIdx.y);
+    float2 *sd = reinterpret_cast<float2 *>(eng2::dyn_smem());
+    const int s = (int)threadIdx.x % SEQ;
+    const int j = (int)threadIdx.x / SEQ;
+    eng2::Job q{s, s & 1, s >> 1, j};
+    {
+        float re[kR0], im[kR0];
+        ld.template load<NZ, 16>(q, re, im);
+        eng2::dft_half_zero<kR0, -1, NZ>(re, im);
+        float4 *p4 = reinterpret_cast<float4 *>(sd + s * RL + eng2::pad16(j * kR0));
+#pragma unroll
+        for (int k = 0; k < 16; ++k) p4[k] = make_float4(re[2 * k], re[2 * k + 1], im[2 * k], im[2 * k + 1]);
+    }
+    __syncthreads();
+    PC Q[16];
+    {
+        const float4 *p4 = reinterpret_cast<const float4 *>(sd + s * RL + 2 * j);
+#pragma unroll
+        for (int r = 0; r < 16; ++r) {
+            const float4 v = p4[eng2::pad16(r * kR0) / 2];
+            Q[r] = {make_float2(v.x, v.y), make_float2(v.z, v.w)};
+        }
+    }
+#pragma unroll
+    for (int r = 1; r < 16; ++r) Q[r] = pk::cmul(Q[r], tw1(tws, r, j));
+    pk::dft16<16>(Q);
+    float re0[16], im0[16], re1[16], im1[16];
+#pragma unroll
+    for (int p = 0; p < 16; ++p) {
+        re0[p] = Q[p].re.x; im0[p] = Q[p].im.x;
+        re1[p] = Q[p].re.y; im1[p] = Q[p].im.y;
+    }
+    eng2::Job q0{s, s & 1, s >> 1, 2 * j}, q1{s, s & 1, s >> 1, 2 * j + 1};
+    st.template store<16, kR0>(q0, re0, im0);
+    st.template store<16, kR0>(q1, re1, im1);
+}
+
 // --------------------------------------------------------------------- pass 2
 // Dynamic shared memory of the packed pass 2 before its mbarrier (8 bytes after
 // it): the exchange of 8 sequences, which also receives the staged tile.

@@ -51,11 +51,14 @@ int launch_two(const Plan &p, int band_idx, const BandDev &b, int64_t s0, int64_
     const bool pk2 = LOGN == 18 && p.packed >= 1 && p.tma && p.p2_threads == 128 && tw->p512_f;
     const bool pk1 = pk2 && p.packed >= 2;
     if constexpr (LOGN == 18) {
-        if (pk1) {
+        if (pk1) {   // packed = 2: both stages paired; 3: scalar first stage, paired second
             const bool z3 = 8 * b.n <= 3 * (int64_t)C1::N;
-            auto k1 = z3 ? p3::k_pass1p<LOGN, 3> : p3::k_pass1p<LOGN, 4>;
-            static bool attr1p[2] = {false, false};
-            if (!attr1p[z3]) { set_smem(k1, C1::SMEM); attr1p[z3] = true; }
+            const bool hy = p.packed == 3;
+            auto k1 = hy ? (z3 ? p3::k_pass1h<LOGN, 3> : p3::k_pass1h<LOGN, 4>)
+                         : (z3 ? p3::k_pass1p<LOGN, 3> : p3::k_pass1p<LOGN, 4>);
+            static bool attr1p[4] = {false, false, false, false};
+            const int ai = (hy ? 2 : 0) + (z3 ? 1 : 0);
+            if (!attr1p[ai]) { set_smem(k1, C1::SMEM); attr1p[ai] = true; }
             k1<<<dim3(C1::TILES, (unsigned)nc), C1::THREADS, C1::SMEM, s>>>(ld1, st1, tw->p512_f);
         }
     }

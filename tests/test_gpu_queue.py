@@ -48,6 +48,7 @@ DEFAULT = {"FSTAT_PERSISTENT": "0"}                       # the default (pass 2 
 FUSED = {"FSTAT_PERSISTENT": "0", "FSTAT_FUSED": "1"}    # two-stage engine, one ticket-ordered launch
 PK1 = {"FSTAT_PERSISTENT": "0", "FSTAT_FUSED": "0", "FSTAT_PACKED": "1"}   # pass 2 paired at 2^18
 PK2 = {"FSTAT_PERSISTENT": "0", "FSTAT_FUSED": "0", "FSTAT_PACKED": "2"}   # both passes paired
+PK3 = {"FSTAT_PERSISTENT": "0", "FSTAT_FUSED": "0", "FSTAT_PACKED": "3"}   # pass 2 and pass-1 stage 1
 
 
 @pytest.mark.parametrize("base,env", [
@@ -63,6 +64,7 @@ PK2 = {"FSTAT_PERSISTENT": "0", "FSTAT_FUSED": "0", "FSTAT_PACKED": "2"}   # bot
     (PK1, {"FSTAT_CELL_BATCH": "7", "FSTAT_STREAMS": "2"}),
     (PK1, {"FSTAT_PF_DIST": "0", "FSTAT_CELL_BATCH": "9"}),
     (PK2, {"FSTAT_PACKED": "2", "FSTAT_CELL_BATCH": "5", "FSTAT_STREAMS": "2"}),
+    (PK3, {"FSTAT_PACKED": "3", "FSTAT_CELL_BATCH": "6"}),
     (TWO, {"FSTAT_TMA": "0"}),
     (TWO, {"FSTAT_P2_THREADS": "256"}),
     (TWO, {"FSTAT_PACKED": "0", "FSTAT_CELL_BATCH": "5", "FSTAT_STREAMS": "2"}),
