@@ -219,8 +219,8 @@ def run_reference(args, rank, world):
 # ----------------------------------------------------------------------------- our arm
 # Files that define the FFT/F-statistic kernels (host orchestration excluded): a
 # change to any of them voids the recorded DRAM traffic.
-KERNEL_SOURCES = ("fft_engine.cuh", "fft_engine2.cuh", "passes.cuh", "passes2.cuh",
-                  "search_launch.cuh", "search_f32.cu", "search_f64.cu", "geometry.cu",
+KERNEL_SOURCES = ("fft_engine.cuh", "fft_engine2.cuh", "passes.cuh", "passes2.cuh", "packed.cuh",
+                  "passes3.cuh", "search_launch.cuh", "search_f32.cu", "search_f64.cu", "geometry.cu",
                   "search_persistent.cu", "sync_ptx.cuh", "fstat_internal.h")
 
 
