@@ -451,6 +451,10 @@ def run_ours(args, rank, world, dist):
     # algorithmic HBM bytes at the measured HBM copy rate
     fma_tf = fstat.measure_fp32_fma(stream.cuda_stream)
     l2_gbs = fstat.measure_l2_copy(32 << 20, stream.cuda_stream)
+    # the same fraction against the FFMA rate measured on this device (the derived
+    # peak above rests on the SM count and lanes per SM)
+    roofline["frac_vs_measured_fma"] = round(achieved / fma_tf, 4)
+    roofline["measured_fma_tflops"] = round(fma_tf, 2)
     hbm_gbs = float(peaks.get("hbm_gbs", 6800.0))
     cells = w.n_sky * w.n_spin * len(w.bands)
     nfft = w.bands[0].n_fft

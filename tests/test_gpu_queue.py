@@ -224,3 +224,34 @@ def test_autotune_keeps_results(fs):
         common = {tuple(x) for x in np.stack([ref[k] for k in keys], 1).tolist()} & \
                  {tuple(x) for x in np.stack([c[k] for k in keys], 1).tolist()}
         assert len(common) >= 0.99 * min(len(ref), len(c))
+
+
+@pytest.mark.parametrize("env", [
+    {"FSTAT_PERSISTENT": "1", "FSTAT_PERSIST_BATCH": "3"},     # warp-specialised persistent kernel
+    {"FSTAT_FUSED": "1", "FSTAT_FUSED_BATCH": "4"},             # queue-fed persistent launch
+    PK2,                                                        # both passes paired
+    PK3,                                                        # pass 2 and pass-1 stage 1 paired
+    TWO,                                                        # scalar two-stage passes
+])
+def test_queue_kernels_against_oracle_every_bin(fs, env):
+    """Every bin of a few cells of a two-sidereal-day band (N = 86164, N_fft =
+    2^18, with a band offset) in each non-default launch form, directly against
+    the FP64 oracle at the FP32 tolerance (not only bitwise against the default)."""
+    import oracle as O
+    w0 = S.workload(1, n_sky=2, n_spin=2)
+    b = S.make_band(86164, 2.0, 404, 1.0, w0.alpha, w0.delta, w0.fdot, [], n_fft=1 << 18,
+                    f_off=100 + (1 - 2 ** -5) * 7)
+    w = S.Workload("queue-oracle", [b], w0.alpha, w0.delta, w0.fdot, 10.0, upsample=2)
+    p, rc, c, total = _run(fs, w, -1.0, env)
+    p.close()
+    nb = (1 << 17) - 1
+    assert rc == fs.FSTAT_OK and total == 4 * nb
+    prm = O.params(w.lat, w.gamma, w.upsample, 0.0, False, 0)
+    cells = [(s, j) for s in range(2) for j in range(2)]
+    ref = O.cells_F(b, prm, w.alpha, w.delta, w.fdot, np.array([x[0] for x in cells]),
+                    np.array([x[1] for x in cells]), 0, 0, os.cpu_count() or 4)
+    for i, (sk, sp) in enumerate(cells):
+        sel = c[(c["sky"] == sk) & (c["spin"] == sp)]
+        assert np.array_equal(sel["bin"], np.arange(1, nb + 1))
+        err = np.abs(sel["F"] - ref[i]) / np.maximum(ref[i], 2.0)
+        assert err.max() <= 1e-4, (env, sk, sp, err.max())
