@@ -212,7 +212,7 @@ void build_twiddles(Plan &p, const std::vector<int> &logs, int &n_alloc) {
         host_twiddles(lg, a, b, c, d);
         stage1_twiddles(log_n1(lg), e);
         stage1_twiddles(log_n2(lg), f);
-        if (lg == 18) packed512_twiddles(g);
+        if (log_n1(lg) == 9) packed512_twiddles(g);   // 512-point rows: N_fft = 2^18, 2^19
         for (auto *v : {&a, &b, &c, &d, &e, &f, &g}) {
             while (hd.size() % 4) hd.push_back(0.0);   // 16-byte aligned float tables
             offs.push_back(hd.size());
@@ -233,7 +233,7 @@ void build_twiddles(Plan &p, const std::vector<int> &logs, int &n_alloc) {
         t.in1_f = df + o[0]; t.in2_f = df + o[1];
         t.lo_f = df + o[2]; t.hi_f = df + o[3];
         t.s1_f = df + o[4]; t.s2_f = df + o[5];
-        if (logs[i] == 18) t.p512_f = reinterpret_cast<const float4 *>(df + o[6]);
+        if (log_n1(logs[i]) == 9) t.p512_f = reinterpret_cast<const float4 *>(df + o[6]);
         p.tw.push_back(t);
     }
 }

@@ -34,7 +34,8 @@ struct TwiddleSet {
     // second engine: stage-1 twiddles W_M^{r j} laid out [r][j], r < R1, j < R0
     // (float), for the rows (M = N1 = R0 R1, pass 2) and the columns (M = N2, pass 1)
     const float *s1_f = nullptr, *s2_f = nullptr;
-    // packed passes (N_fft = 2^18): stage-1 twiddles of a 512-point pass as pairs,
+    // packed passes (512-point rows, N_fft = 2^18 and 2^19): stage-1 twiddles of a
+    // 512-point pass as pairs,
     // [r][k] = (cos a_2k, cos a_2k+1, -sin a_2k, -sin a_2k+1), a_j = 2 pi r j / 512
     const float4 *p512_f = nullptr;
 };

@@ -1,6 +1,6 @@
-// The FP32 search passes in packed arithmetic (packed.cuh) for transforms whose
-// two passes have length 512 (N_fft = 2^18: N1 = N2 = 512), the length of the
-// two-sidereal-day segments.  Same four-step split, scratch layout, tiles and
+// The FP32 search passes in packed arithmetic (packed.cuh) for passes of length
+// 512: both passes at N_fft = 2^18 (N1 = N2 = 512, the two-sidereal-day
+// segments), the rows (pass 2) at 2^19.  Same four-step split, scratch layout, tiles and
 // launch shapes as the second engine's passes (passes2.cuh); what changes is how
 // a thread's 32 elements are transformed:
 //

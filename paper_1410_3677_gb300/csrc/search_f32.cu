@@ -47,9 +47,10 @@ int launch_two(const Plan &p, int band_idx, const BandDev &b, int64_t s0, int64_
                const TwiddleSet *tw) {
     using C1 = Cfg2<LOGN, 1>;
     using C2 = Cfg2<LOGN, 2>;
-    // N_fft = 2^18: pass 2 (and, with packed = 2, pass 1) in paired FP32 arithmetic
-    const bool pk2 = LOGN == 18 && p.packed >= 1 && p.tma && p.p2_threads == 128 && tw->p512_f;
-    const bool pk1 = pk2 && p.packed >= 2;
+    // 512-point rows (N_fft = 2^18, 2^19): pass 2 in paired FP32 arithmetic; at 2^18
+    // (512-point columns) also pass 1 with packed = 2 or 3
+    const bool pk2 = (LOGN == 18 || LOGN == 19) && p.packed >= 1 && p.tma && p.p2_threads == 128 && tw->p512_f;
+    const bool pk1 = pk2 && LOGN == 18 && p.packed >= 2;
     if constexpr (LOGN == 18) {
         if (pk1) {   // packed = 2: both stages paired; 3: scalar first stage, paired second
             const bool z3 = 8 * b.n <= 3 * (int64_t)C1::N;
@@ -80,7 +81,7 @@ int launch_two(const Plan &p, int band_idx, const BandDev &b, int64_t s0, int64_
         k1<<<dim3(C1::TILES, (unsigned)nc), C1::THREADS, C1::SMEM, s>>>(ld1, st1, tw->s2_f);
     }
     if (mid) record_timing_event(mid, s);
-    if constexpr (LOGN == 18) {
+    if constexpr (LOGN == 18 || LOGN == 19) {
         if (pk2) {
             using D2 = Cfg2<LOGN, 2, 128>;
             ScratchLoadTMA<D2> lt{};
