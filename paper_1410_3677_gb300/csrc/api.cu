@@ -380,7 +380,7 @@ void create_impl(Plan &p, const fstat_plan_desc *d) {
         // and keeps the per-launch event timings free of overlap
         p.n_workers = 1;
         if (const char *v = getenv("FSTAT_STREAMS")) p.n_workers = std::max(1, std::min(8, atoi(v)));
-        const int64_t budget = int64_t(4) << 30;     // per worker slot
+        const int64_t budget = int64_t(16) << 30;    // per worker slot (a sky batch of 2^18 cells)
         p.cell_batch = std::max<int64_t>(1, std::min<int64_t>(4096, budget / (2 * max_nfft * (int64_t)tsz)));
         p.cell_batch = std::min<int64_t>(p.cell_batch, p.sky_batch * d->n_spin);
         if (const char *v = getenv("FSTAT_CELL_BATCH")) p.cell_batch = std::max(1, std::min(65535, atoi(v)));
@@ -399,6 +399,7 @@ void create_impl(Plan &p, const fstat_plan_desc *d) {
             p.pf_dist = 3 * (int64_t)sms;
         }
         if (const char *v = getenv("FSTAT_PF_DIST")) p.pf_dist = std::max(0, atoi(v));
+        if (const char *v = getenv("FSTAT_PF_DIST_PAIRED")) p.pf_dist_pk = std::max(0, atoi(v));
         if (const char *v = getenv("FSTAT_TMA")) p.tma = atoi(v) != 0;
         if (const char *v = getenv("FSTAT_PACKED")) p.packed = std::max(0, std::min(3, atoi(v)));
         if (const char *v = getenv("FSTAT_P2_THREADS")) p.p2_threads = atoi(v) == 128 ? 128 : 256;

@@ -87,7 +87,7 @@ int launch_two(const Plan &p, int band_idx, const BandDev &b, int64_t s0, int64_
             ScratchLoadTMA<D2> lt{};
             lt.scratch = ld2.scratch;
             lt.tw = ld2.tw;
-            lt.pf_dist = 2 * ld2.pf_dist;
+            lt.pf_dist = p.pf_dist_pk;   // the paired pass gains nothing from L2 prefetch ahead
             lt.err = p.qerr;
             const auto ep = make_epi<LOGN, LOWER, 128>(p, band_idx, b, c0, s0, cb);
             auto k2 = p3::k_pass2p<LOGN, LOWER>;
