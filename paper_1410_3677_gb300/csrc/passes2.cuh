@@ -88,6 +88,48 @@ struct SearchLoad2 {
     }
 };
 
+// The same input with the spindown phase shared by the two lanes of a column
+// (column mapping: lanes 2f and 2f + 1 hold the a and b halves of the same
+// samples): each lane evaluates the phase of every other element, r = 2 i + t,
+// and both read each element's (cos, sin) from the lane that evaluated it.
+template <class C>
+struct SearchLoad2S : SearchLoad2<C> {
+    template <int R, int JPF>
+    __device__ __forceinline__ void load(const eng2::Job &q, float *re, float *im) const {
+        static_assert(R % 2 == 0, "elements in pairs");
+        const int kb = this->k1_0 + q.f + C::N1 * q.j;
+#pragma unroll
+        for (int r = 0; r < R; ++r) {      // loads first: all in flight together
+            const int k = kb + C::N1 * JPF * r;
+            float2 v = make_float2(0.f, 0.f);
+            if (k < this->n) v = __ldg(this->ws + 2 * k + q.t);
+            re[r] = v.x; im[r] = v.y;
+        }
+        float cs[R / 2], sn[R / 2];
+        const int kt = kb + C::N1 * JPF * q.t;
+#pragma unroll
+        for (int i = 0; i < R / 2; ++i) {   // this lane's half of the phases
+            const uint32_t k = (uint32_t)(kt + C::N1 * JPF * 2 * i);
+            const uint64_t kk = (uint64_t)k * (uint64_t)k;
+            const int32_t top = (int32_t)((this->afx * kk) >> 32);   // cycles in [-1/2, 1/2)
+            __sincosf((float)top * 1.4629180792671596e-09f, &sn[i], &cs[i]);   // 2 pi / 2^32
+        }
+        const int lane = (int)threadIdx.x & 31;
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int src = (lane & ~1) | (r & 1);   // the lane that evaluated element r
+            const float c = __shfl_sync(0xffffffffu, cs[r / 2], src);
+            const float sv = __shfl_sync(0xffffffffu, sn[r / 2], src);
+            const uint32_t k = (uint32_t)(kb + C::N1 * JPF * r);
+            if (k < (uint32_t)this->n) {
+                const float x = re[r], y = im[r];
+                re[r] = x * c + y * sv;
+                im[r] = y * c - x * sv;
+            }
+        }
+    }
+};
+
 // The four-step twiddle W_N^{k1 l2} between the passes, applied by the pass-2
 // loaders to the elements k1 = j + r JPF of row l2 as W^{l2 j} (W^{l2 JPF})^r,
 // the two factors from the tables W_N^m = hi[m >> log N1] lo[m & (N1 - 1)].

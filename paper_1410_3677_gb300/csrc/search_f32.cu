@@ -66,6 +66,15 @@ int launch_two(const Plan &p, int band_idx, const BandDev &b, int64_t s0, int64_
     // columns known zero beyond 3/8 of their length (radix-32 first stage) or 1/2
     bool launched = pk1;
     if constexpr (eng2::radix0(C1::M) == 32) {
+        if (!launched && 8 * b.n <= 3 * (int64_t)C1::N && p.share_chirp) {
+            SearchLoad2S<C1> l1s{};
+            static_cast<SearchLoad2<C1> &>(l1s) = ld1;
+            auto k1 = k_pass2<LOGN, 1, eng2::kMapFJ, SearchLoad2S<C1>, ScratchStore2<C1>, 256, 3>;
+            static bool attr3s = false;
+            if (!attr3s) { set_smem(k1, C1::SMEM); attr3s = true; }
+            k1<<<dim3(C1::TILES, (unsigned)nc), C1::THREADS, C1::SMEM, s>>>(l1s, st1, tw->s2_f);
+            launched = true;
+        }
         if (!launched && 8 * b.n <= 3 * (int64_t)C1::N) {
             auto k1 = k_pass2<LOGN, 1, eng2::kMapFJ, SearchLoad2<C1>, ScratchStore2<C1>, 256, 3>;
             static bool attr3 = false;
@@ -73,6 +82,15 @@ int launch_two(const Plan &p, int band_idx, const BandDev &b, int64_t s0, int64_
             k1<<<dim3(C1::TILES, (unsigned)nc), C1::THREADS, C1::SMEM, s>>>(ld1, st1, tw->s2_f);
             launched = true;
         }
+    }
+    if (!launched && p.share_chirp) {
+        SearchLoad2S<C1> l1s{};
+        static_cast<SearchLoad2<C1> &>(l1s) = ld1;
+        auto k1 = k_pass2<LOGN, 1, eng2::kMapFJ, SearchLoad2S<C1>, ScratchStore2<C1>, 256, 4>;
+        static bool attr1s = false;
+        if (!attr1s) { set_smem(k1, C1::SMEM); attr1s = true; }
+        k1<<<dim3(C1::TILES, (unsigned)nc), C1::THREADS, C1::SMEM, s>>>(l1s, st1, tw->s2_f);
+        launched = true;
     }
     if (!launched) {
         auto k1 = k_pass2<LOGN, 1, eng2::kMapFJ, SearchLoad2<C1>, ScratchStore2<C1>, 256, 4>;

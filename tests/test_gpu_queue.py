@@ -65,6 +65,7 @@ PK3 = {"FSTAT_PERSISTENT": "0", "FSTAT_FUSED": "0", "FSTAT_PACKED": "3"}   # pas
     (PK1, {"FSTAT_PF_DIST": "0", "FSTAT_CELL_BATCH": "9"}),
     (PK2, {"FSTAT_PACKED": "2", "FSTAT_CELL_BATCH": "5", "FSTAT_STREAMS": "2"}),
     (PK3, {"FSTAT_PACKED": "3", "FSTAT_CELL_BATCH": "6"}),
+    (TWO, {"FSTAT_PACKED": "0", "FSTAT_SHARE_CHIRP": "0"}),   # each lane its own spindown phases
     (TWO, {"FSTAT_TMA": "0"}),
     (TWO, {"FSTAT_P2_THREADS": "256"}),
     (TWO, {"FSTAT_PACKED": "0", "FSTAT_CELL_BATCH": "5", "FSTAT_STREAMS": "2"}),
