@@ -482,7 +482,7 @@ def run_ours(args, rank, world, dist):
                         "basis": "2 transforms x 5 N log2 N FLOP; scratch written and read once (2 x 2 x N x 8 B) "
                                  "through L2; HBM: the sky's w (16 B per sample) shared by its spindowns + 16 B "
                                  "per candidate; the as-run DRAM term uses the measured traffic of both passes "
-                                 "(the scratch of 1024-cell launches reaches DRAM)"}
+                                 "(the scratch of a launch is larger than L2 and reaches DRAM)"}
 
     # ---------------------------------------------------------------- plain FP64 form on a subgrid
     fp64 = None
