@@ -312,7 +312,8 @@ fstat_status fstat_lattice_grid(const fstat_lattice *lattice, double *alpha, dou
    call before any stream capture.  Every call shares the arrays and nothing in
    them has to start at zero (each call writes the whole intermediate it reads);
    calls that overlap on the GPU (other streams, other host threads) race on them.
-   Every call ends by synchronising cuda_stream with the host.  The addresses and
+   Every call ends by synchronising cuda_stream with the host, so no call may be
+   made while a stream capture is active on cuda_stream.  The addresses and
    the filled-table flags are cached per device for the life of the process: after
    a cudaDeviceReset of a device the cache is stale, and this entry point must not
    be called on that device again.  Returns FSTAT_ERR_ARG for a NULL or misaligned

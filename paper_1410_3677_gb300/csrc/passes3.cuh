@@ -28,11 +28,6 @@ using pk::PC;
 
 constexpr int kM = 512;          // pass length (both passes at N_fft = 2^18)
 constexpr int kR0 = 32, kR1 = 16;
-// Pass-2 exchange: per sequence 16 stage-1 job pairs x 16 elements, 16-byte
-// words, rows of 17 words so that the 8 lanes of a quarter-warp reading the same
-// element of consecutive job pairs fall in 8 different bank groups.
-constexpr int kRowW = 17;
-constexpr int kSeqW = 16 * kRowW;   // 16-byte words per sequence
 
 // Stage-1 twiddles of a 512-point pass as packed pairs: entry [r][k] =
 // (cos a_{2k}, cos a_{2k+1}, -sin a_{2k}, -sin a_{2k+1}), a_j = 2 pi r j / 512,
@@ -167,10 +162,13 @@ k_pass1h(SearchLoad2<Cfg2<LOGN, 1>> ld, ScratchStore2<Cfg2<LOGN, 1>> st, const f
 
 // --------------------------------------------------------------------- pass 2
 // Dynamic shared memory of the packed pass 2 before its mbarrier (8 bytes after
-// it): the exchange of 8 sequences, which also receives the staged tile.
+// it): the staged tile, 4 rows x 2 transforms x 512 complex floats.  Each warp's
+// exchange lies over the row it has staged: 2 transforms x 16 job pairs x 16
+// elements of 16 bytes, exactly the row's 8 KiB, so no warp waits for another
+// between the stages.
 template <class C>
 __host__ __device__ constexpr size_t pass2p_smem() {
-    return (size_t)C::SEQ * kSeqW * 16;
+    return (size_t)2 * C::F * C::N1 * sizeof(float2);
 }
 
 // Rows l2 of the scratch, staged by a bulk copy (ScratchLoadTMA's copy and
@@ -259,13 +257,13 @@ k_pass2p(ScratchLoadTMA<Cfg2<LOGN, 2, 128>> ld, SearchEpi2<Cfg2<LOGN, 2, 128>, L
          const float4 *__restrict__ tws) {
     using C = Cfg2<LOGN, 2, 128>;
     static_assert(C::M == kM && C::SEQ == 8 && C::F == 4 && C::TPF == 16, "512-point rows, 4-row tiles");
-    static_assert(2 * C::F * C::N1 * sizeof(float2) <= pass2p_smem<C>(), "the staged tile fits the exchange area");
+    static_assert(2 * kR1 * kR1 * 16 == 2 * C::N1 * sizeof(float2), "a warp's exchange fills its staged row");
     ld.prefetch_ahead();
     ld.init(blockIdx.x, blockIdx.y, blockIdx.y);
-    ld.bar = reinterpret_cast<uint64_t *>(eng2::dyn_smem() + pass2p_smem<C>());   // after this exchange
+    ld.bar = reinterpret_cast<uint64_t *>(eng2::dyn_smem() + pass2p_smem<C>());   // after the staged tile
+    const int w = (int)threadIdx.x >> 5, lane = (int)threadIdx.x & 31;
     ep.init(blockIdx.x, blockIdx.y, blockIdx.y);
     ld.stage();
-    const int w = (int)threadIdx.x >> 5, lane = (int)threadIdx.x & 31;
     const int t = lane >> 4;           // transform
     const int j = lane & 15;           // stage-0 butterfly; stage-1 job pair (2j, 2j + 1)
     const int f = w;                   // tile row
@@ -301,15 +299,20 @@ k_pass2p(ScratchLoadTMA<Cfg2<LOGN, 2, 128>> ld, SearchEpi2<Cfg2<LOGN, 2, 128>, L
         }
     }
     pk::dft16<16>(P);   // P[k] = (X_{2k}, X_{2k+1}) of row l2
-    __syncthreads();    // every warp has read its staged rows: the exchange may be overwritten
-    float4 *ex = reinterpret_cast<float4 *>(eng2::dyn_smem()) + (t * C::F + f) * kSeqW;
+    // the warp's exchange covers exactly the row f it has just read: only its own
+    // lanes have to be done reading
+    __syncwarp();
+    float4 *ex = reinterpret_cast<float4 *>(eng2::dyn_smem()) + (2 * f + t) * (kR1 * kR1);
+    // element (k, j) at word 16 k + (j ^ k): the 8 lanes of a quarter-warp fall in
+    // 8 different 16-byte bank groups both when storing (fixed k) and when
+    // loading (fixed r)
 #pragma unroll
-    for (int k = 0; k < 16; ++k) ex[k * kRowW + j] = make_float4(P[k].re.x, P[k].re.y, P[k].im.x, P[k].im.y);
+    for (int k = 0; k < 16; ++k) ex[k * 16 + (j ^ k)] = make_float4(P[k].re.x, P[k].re.y, P[k].im.x, P[k].im.y);
     __syncwarp();
     PC Q[16];
 #pragma unroll
     for (int r = 0; r < 16; ++r) {
-        const float4 v = ex[j * kRowW + r];
+        const float4 v = ex[j * 16 + (r ^ j)];
         Q[r] = {make_float2(v.x, v.y), make_float2(v.z, v.w)};
     }
 #pragma unroll

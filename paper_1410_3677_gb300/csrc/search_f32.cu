@@ -109,7 +109,7 @@ int launch_two(const Plan &p, int band_idx, const BandDev &b, int64_t s0, int64_
             lt.err = p.qerr;
             const auto ep = make_epi<LOGN, LOWER, 128>(p, band_idx, b, c0, s0, cb);
             auto k2 = p3::k_pass2p<LOGN, LOWER>;
-            constexpr size_t smem2 = p3::pass2p_smem<D2>() + 16;   // exchange + mbarrier
+            constexpr size_t smem2 = p3::pass2p_smem<D2>() + 16;   // staged tile + mbarrier
             static bool attr2p = false;
             if (!attr2p) { set_smem(k2, smem2); attr2p = true; }
             k2<<<dim3(D2::TILES, (unsigned)nc), D2::THREADS, smem2, s>>>(lt, ep, tw->p512_f);
