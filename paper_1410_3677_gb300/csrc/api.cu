@@ -401,6 +401,10 @@ void create_impl(Plan &p, const fstat_plan_desc *d) {
         if (const char *v = getenv("FSTAT_PF_DIST")) p.pf_dist = std::max(0, atoi(v));
         if (const char *v = getenv("FSTAT_PF_DIST_PAIRED")) p.pf_dist_pk = std::max(0, atoi(v));
         if (const char *v = getenv("FSTAT_SHARE_CHIRP")) p.share_chirp = atoi(v) != 0;
+        if (const char *v = getenv("FSTAT_P2_TS")) {
+            const int ts = atoi(v);
+            p.p2_ts = ts == 64 || ts == 128 ? ts : 32;
+        }
         if (const char *v = getenv("FSTAT_TMA")) p.tma = atoi(v) != 0;
         if (const char *v = getenv("FSTAT_PACKED")) p.packed = std::max(0, std::min(3, atoi(v)));
         if (const char *v = getenv("FSTAT_P2_THREADS")) p.p2_threads = atoi(v) == 128 ? 128 : 256;

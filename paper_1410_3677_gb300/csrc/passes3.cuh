@@ -162,7 +162,7 @@ k_pass1h(SearchLoad2<Cfg2<LOGN, 1>> ld, ScratchStore2<Cfg2<LOGN, 1>> st, const f
 
 // --------------------------------------------------------------------- pass 2
 // Dynamic shared memory of the packed pass 2 before its mbarrier (8 bytes after
-// it): the staged tile, 4 rows x 2 transforms x 512 complex floats.  Each warp's
+// it): the staged tile, F rows x 2 transforms x 512 complex floats.  Each warp's
 // exchange lies over the row it has staged: 2 transforms x 16 job pairs x 16
 // elements of 16 bytes, exactly the row's 8 KiB, so no warp waits for another
 // between the stages.
@@ -171,10 +171,6 @@ __host__ __device__ constexpr size_t pass2p_smem() {
     return (size_t)2 * C::F * C::N1 * sizeof(float2);
 }
 
-// Rows l2 of the scratch, staged by a bulk copy (ScratchLoadTMA's copy and
-// bounded wait), four-step twiddle folded into the split, packed row DFTs, then
-// F, threshold and compaction.  128 threads: 4 rows x 2 transforms, a warp per
-// row (F_a in lanes 0-15, F_b in lanes 16-31).
 // F per bin of the packed outputs (the epilogue of SearchEpi2 on pairs of jobs).
 // Lanes l (F_a) and l ^ 16 (F_b) hold the same bins; the a lane evaluates F on
 // the outputs p < H, the b lane on p >= H, each taking the partner's values for
@@ -251,12 +247,17 @@ __device__ __forceinline__ void epilogue(const SearchEpi2<C, LOWER> &ep, int t, 
         }
 }
 
-template <int LOGN, bool LOWER>
-__global__ void __launch_bounds__(128, 6)
-k_pass2p(ScratchLoadTMA<Cfg2<LOGN, 2, 128>> ld, SearchEpi2<Cfg2<LOGN, 2, 128>, LOWER> ep,
+// Rows l2 of the scratch, staged by a bulk copy (ScratchLoadTMA's copy and
+// bounded wait), four-step twiddle folded into the split, packed row DFTs, then
+// F, threshold and compaction.  A warp per row (F_a in lanes 0-15, F_b in lanes
+// 16-31), TS / 32 rows per CTA; with one row per CTA (TS = 32, the default) 24
+// CTAs share an SM and each waits only for its own 8 KiB copy.
+template <int LOGN, bool LOWER, int TS = 32>
+__global__ void __launch_bounds__(TS, 768 / TS)
+k_pass2p(ScratchLoadTMA<Cfg2<LOGN, 2, TS>> ld, SearchEpi2<Cfg2<LOGN, 2, TS>, LOWER> ep,
          const float4 *__restrict__ tws) {
-    using C = Cfg2<LOGN, 2, 128>;
-    static_assert(C::M == kM && C::SEQ == 8 && C::F == 4 && C::TPF == 16, "512-point rows, 4-row tiles");
+    using C = Cfg2<LOGN, 2, TS>;
+    static_assert(C::M == kM && C::F == TS / 32 && C::SEQ == 2 * C::F && C::TPF == 16, "512-point rows, a warp per row");
     static_assert(2 * kR1 * kR1 * 16 == 2 * C::N1 * sizeof(float2), "a warp's exchange fills its staged row");
     ld.prefetch_ahead();
     ld.init(blockIdx.x, blockIdx.y, blockIdx.y);

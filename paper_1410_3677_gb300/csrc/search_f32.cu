@@ -40,6 +40,25 @@ void launch_pass2(const Plan &p, int band_idx, const BandDev &b, int64_t s0, int
     k2<<<dim3(C2::TILES, (unsigned)nc), C2::THREADS, C2::SMEM + extra, s>>>(ld2, st2, tw->s1_f);
 }
 
+// The paired pass 2 (512-point rows) in CTAs of TS / 32 rows, one warp per row.
+template <int LOGN, bool LOWER, int TS>
+void launch_pass2p(const Plan &p, int band_idx, const BandDev &b, int64_t s0, int64_t c0, int64_t nc,
+                   cudaStream_t s, const CellBufs &cb, const ScratchLoad2<Cfg2<LOGN, 2>> &ld2,
+                   const TwiddleSet *tw) {
+    using D2 = Cfg2<LOGN, 2, TS>;
+    ScratchLoadTMA<D2> lt{};
+    lt.scratch = ld2.scratch;
+    lt.tw = ld2.tw;
+    lt.pf_dist = p.pf_dist_pk;   // the paired pass gains nothing from L2 prefetch ahead
+    lt.err = p.qerr;
+    const auto ep = make_epi<LOGN, LOWER, TS>(p, band_idx, b, c0, s0, cb);
+    auto k2 = p3::k_pass2p<LOGN, LOWER, TS>;
+    constexpr size_t smem2 = p3::pass2p_smem<D2>() + 16;   // staged tile + mbarrier
+    static bool attr2p = false;
+    if (!attr2p) { set_smem(k2, smem2); attr2p = true; }
+    k2<<<dim3(D2::TILES, (unsigned)nc), D2::THREADS, smem2, s>>>(lt, ep, tw->p512_f);
+}
+
 template <int LOGN, bool LOWER>
 int launch_two(const Plan &p, int band_idx, const BandDev &b, int64_t s0, int64_t c0, int64_t nc,
                cudaStream_t s, cudaEvent_t mid, const CellBufs &cb, const SearchLoad2<Cfg2<LOGN, 1>> &ld1,
@@ -101,18 +120,9 @@ int launch_two(const Plan &p, int band_idx, const BandDev &b, int64_t s0, int64_
     if (mid) record_timing_event(mid, s);
     if constexpr (LOGN == 18 || LOGN == 19) {
         if (pk2) {
-            using D2 = Cfg2<LOGN, 2, 128>;
-            ScratchLoadTMA<D2> lt{};
-            lt.scratch = ld2.scratch;
-            lt.tw = ld2.tw;
-            lt.pf_dist = p.pf_dist_pk;   // the paired pass gains nothing from L2 prefetch ahead
-            lt.err = p.qerr;
-            const auto ep = make_epi<LOGN, LOWER, 128>(p, band_idx, b, c0, s0, cb);
-            auto k2 = p3::k_pass2p<LOGN, LOWER>;
-            constexpr size_t smem2 = p3::pass2p_smem<D2>() + 16;   // staged tile + mbarrier
-            static bool attr2p = false;
-            if (!attr2p) { set_smem(k2, smem2); attr2p = true; }
-            k2<<<dim3(D2::TILES, (unsigned)nc), D2::THREADS, smem2, s>>>(lt, ep, tw->p512_f);
+            if (p.p2_ts == 32) launch_pass2p<LOGN, LOWER, 32>(p, band_idx, b, s0, c0, nc, s, cb, ld2, tw);
+            else if (p.p2_ts == 64) launch_pass2p<LOGN, LOWER, 64>(p, band_idx, b, s0, c0, nc, s, cb, ld2, tw);
+            else launch_pass2p<LOGN, LOWER, 128>(p, band_idx, b, s0, c0, nc, s, cb, ld2, tw);
             return 2;
         }
     }

@@ -65,6 +65,8 @@ PK3 = {"FSTAT_PERSISTENT": "0", "FSTAT_FUSED": "0", "FSTAT_PACKED": "3"}   # pas
     (PK1, {"FSTAT_PF_DIST": "0", "FSTAT_CELL_BATCH": "9"}),
     (PK2, {"FSTAT_PACKED": "2", "FSTAT_CELL_BATCH": "5", "FSTAT_STREAMS": "2"}),
     (PK3, {"FSTAT_PACKED": "3", "FSTAT_CELL_BATCH": "6"}),
+    (PK1, {"FSTAT_P2_TS": "128"}),                            # paired pass 2: four rows per CTA
+    (PK1, {"FSTAT_P2_TS": "64", "FSTAT_CELL_BATCH": "7"}),    # two rows per CTA
     (TWO, {"FSTAT_PACKED": "0", "FSTAT_SHARE_CHIRP": "0"}),   # each lane its own spindown phases
     (TWO, {"FSTAT_TMA": "0"}),
     (TWO, {"FSTAT_P2_THREADS": "256"}),
@@ -232,6 +234,7 @@ def test_autotune_keeps_results(fs):
     {"FSTAT_FUSED": "1", "FSTAT_FUSED_BATCH": "4"},             # queue-fed persistent launch
     PK2,                                                        # both passes paired
     PK3,                                                        # pass 2 and pass-1 stage 1 paired
+    {"FSTAT_P2_TS": "128"},                                     # paired pass 2, four rows per CTA
     TWO,                                                        # scalar two-stage passes
 ])
 def test_queue_kernels_against_oracle_every_bin(fs, env):
