@@ -172,7 +172,7 @@ __host__ __device__ constexpr size_t pass2p_smem() {
 }
 
 // F per bin of the packed outputs (the epilogue of SearchEpi2 on pairs of jobs).
-// Lanes l (F_a) and l ^ 16 (F_b) hold the same bins; the a lane evaluates F on
+// Lanes 2j (F_a) and 2j + 1 (F_b) hold the same bins; the a lane evaluates F on
 // the outputs p < H, the b lane on p >= H, each taking the partner's values for
 // its half with one shuffle per value.
 template <class C, bool LOWER>
@@ -190,10 +190,10 @@ __device__ __forceinline__ void epilogue(const SearchEpi2<C, LOWER> &ep, int t, 
         if (full) {
             const PC send = t == 0 ? hi : lo, mine = t == 0 ? lo : hi;
             PC oth;
-            oth.re.x = __shfl_xor_sync(0xffffffffu, send.re.x, 16);
-            oth.re.y = __shfl_xor_sync(0xffffffffu, send.re.y, 16);
-            oth.im.x = __shfl_xor_sync(0xffffffffu, send.im.x, 16);
-            oth.im.y = __shfl_xor_sync(0xffffffffu, send.im.y, 16);
+            oth.re.x = __shfl_xor_sync(0xffffffffu, send.re.x, 1);
+            oth.re.y = __shfl_xor_sync(0xffffffffu, send.re.y, 1);
+            oth.im.x = __shfl_xor_sync(0xffffffffu, send.im.x, 1);
+            oth.im.y = __shfl_xor_sync(0xffffffffu, send.im.y, 1);
             const PC a = t == 0 ? mine : oth, b = t == 0 ? oth : mine;
             const float2 pa = pk::pfma(a.re, a.re, pk::pmul(a.im, a.im));
             const float2 pb = pk::pfma(b.re, b.re, pk::pmul(b.im, b.im));
@@ -204,8 +204,8 @@ __device__ __forceinline__ void epilogue(const SearchEpi2<C, LOWER> &ep, int t, 
             const float2 phi = pk::pfma(hi.re, hi.re, pk::pmul(hi.im, hi.im));
             const float2 ps = t == 0 ? phi : plo, pm = t == 0 ? plo : phi;
             float2 po;
-            po.x = __shfl_xor_sync(0xffffffffu, ps.x, 16);
-            po.y = __shfl_xor_sync(0xffffffffu, ps.y, 16);
+            po.x = __shfl_xor_sync(0xffffffffu, ps.x, 1);
+            po.y = __shfl_xor_sync(0xffffffffu, ps.y, 1);
             const float2 pa = t == 0 ? pm : po, pb = t == 0 ? po : pm;
             Fv[u] = pk::pfma(pa, pk::bc(ep.na), pk::pmul(pb, pk::bc(ep.nb)));
         }
@@ -249,9 +249,9 @@ __device__ __forceinline__ void epilogue(const SearchEpi2<C, LOWER> &ep, int t, 
 
 // Rows l2 of the scratch, staged by a bulk copy (ScratchLoadTMA's copy and
 // bounded wait), four-step twiddle folded into the split, packed row DFTs, then
-// F, threshold and compaction.  A warp per row (F_a in lanes 0-15, F_b in lanes
-// 16-31), TS / 32 rows per CTA; with one row per CTA (TS = 32, the default) 24
-// CTAs share an SM and each waits only for its own 8 KiB copy.
+// F, threshold and compaction.  A warp per row (F_a in the even lanes, F_b in
+// the odd ones), TS / 32 rows per CTA; with one row per CTA (TS = 32, the
+// default) 24 CTAs share an SM and each waits only for its own 8 KiB copy.
 template <int LOGN, bool LOWER, int TS = 32>
 __global__ void __launch_bounds__(TS, 768 / TS)
 k_pass2p(ScratchLoadTMA<Cfg2<LOGN, 2, TS>> ld, SearchEpi2<Cfg2<LOGN, 2, TS>, LOWER> ep,
@@ -265,8 +265,10 @@ k_pass2p(ScratchLoadTMA<Cfg2<LOGN, 2, TS>> ld, SearchEpi2<Cfg2<LOGN, 2, TS>, LOW
     const int w = (int)threadIdx.x >> 5, lane = (int)threadIdx.x & 31;
     ep.init(blockIdx.x, blockIdx.y, blockIdx.y);
     ld.stage();
-    const int t = lane >> 4;           // transform
-    const int j = lane & 15;           // stage-0 butterfly; stage-1 job pair (2j, 2j + 1)
+    // lane 2j + t: a warp's loads from the staged row cover 32 consecutive
+    // complex floats (F_a and F_b of 16 k1), free of bank conflicts
+    const int t = lane & 1;            // transform
+    const int j = lane >> 1;           // stage-0 butterfly; stage-1 job pair (2j, 2j + 1)
     const int f = w;                   // tile row
     const int l2 = ld.l2_0 + f;
     // four-step factors: T_0 = W^{l2 j}, step W^{16 l2}, c = W^{256 l2}
@@ -304,16 +306,17 @@ k_pass2p(ScratchLoadTMA<Cfg2<LOGN, 2, TS>> ld, SearchEpi2<Cfg2<LOGN, 2, TS>, LOW
     // lanes have to be done reading
     __syncwarp();
     float4 *ex = reinterpret_cast<float4 *>(eng2::dyn_smem()) + (2 * f + t) * (kR1 * kR1);
-    // element (k, j) at word 16 k + (j ^ k): the 8 lanes of a quarter-warp fall in
-    // 8 different 16-byte bank groups both when storing (fixed k) and when
-    // loading (fixed r)
+    // element (k, j) at word 16 k + (j ^ 4t ^ k): a quarter-warp holds 4 j of both
+    // transforms, and its 8 lanes fall in 8 different 16-byte bank groups both
+    // when storing (fixed k) and when loading (fixed r)
+    const int jx = j ^ (4 * t);
 #pragma unroll
-    for (int k = 0; k < 16; ++k) ex[k * 16 + (j ^ k)] = make_float4(P[k].re.x, P[k].re.y, P[k].im.x, P[k].im.y);
+    for (int k = 0; k < 16; ++k) ex[k * 16 + (jx ^ k)] = make_float4(P[k].re.x, P[k].re.y, P[k].im.x, P[k].im.y);
     __syncwarp();
     PC Q[16];
 #pragma unroll
     for (int r = 0; r < 16; ++r) {
-        const float4 v = ex[j * 16 + (r ^ j)];
+        const float4 v = ex[j * 16 + (r ^ jx)];
         Q[r] = {make_float2(v.x, v.y), make_float2(v.z, v.w)};
     }
 #pragma unroll
