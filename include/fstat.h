@@ -222,7 +222,8 @@ fstat_status fstat_plan_kernel_stats(const fstat_plan *plan, fstat_kernel_stat *
    counterpart; it picks the GPU-side shapes the search runs with).  It times
    whole searches over the cells [0, sample_cells) (clamped to the grid) with
    CUDA events, changing one choice at a time -- FFT engine (two-stage radix
-   32x16 / radix-8 Stockham), pass-2 tile (128 or 256 threads) and loader (bulk
+   32x16 / radix-8 Stockham), pass-2 tile (128 or 256 threads; one or four rows
+   per CTA for the paired 512-point rows) and loader (bulk
    copies or per-thread loads with L2 prefetch), cells per launch pair, one fused
    ticket-ordered launch or two launches, and at N_fft = 2^18 the passes in
    paired FP32 instructions (two values per instruction: none, pass 2 only, or
@@ -237,7 +238,8 @@ typedef struct {
     int32_t engine;          /* 2: two-stage engine, 1: radix-8 engine; 3: two-stage with
                                 pass 2 in paired FP32 instructions at N_fft = 2^18, 4: with
                                 both passes paired */
-    int32_t pass2_threads;   /* 128 or 256 */
+    int32_t pass2_threads;   /* threads per pass-2 CTA: 32 (one row) or 128 for the paired
+                                512-point rows, 128 or 256 for the scalar pass 2 */
     int32_t pass2_bulk_copy; /* 1: bulk-copy staging, 0: per-thread loads */
     int32_t fused;           /* 1: one ticket-ordered launch per batch */
     int64_t cells_per_launch;

@@ -1200,6 +1200,8 @@ fstat_status fstat_plan_autotune(fstat_plan *p, int64_t sample_cells, fstat_tuni
         (void)cb0;
         { const int old = p->p2_threads;
           try_set([&] { p->p2_threads = old == 128 ? 256 : 128; }, [&] { p->p2_threads = old; }); }
+        { const int old = p->p2_ts;   // the paired rows: one or four rows per CTA
+          try_set([&] { p->p2_ts = old == 32 ? 128 : 32; }, [&] { p->p2_ts = old; }); }
         { const bool old = p->tma;
           try_set([&] { p->tma = !old; }, [&] { p->tma = old; }); }
         { const bool old = p->fused;
@@ -1219,8 +1221,11 @@ fstat_status fstat_plan_autotune(fstat_plan *p, int64_t sample_cells, fstat_tuni
         p->searched = false;
         p->prev_begin = p->prev_end = -1;
         if (chosen) {
-            chosen->engine = p->engine == 2 && p->packed ? 2 + p->packed : p->engine;
-            chosen->pass2_threads = p->p2_threads;
+            // the paired pass 2 (512-point rows) runs whenever packed >= 1 with the
+            // bulk-copy loader and 128-thread scalar tiles
+            const bool paired2 = p->packed >= 1 && p->tma && p->p2_threads == 128;
+            chosen->engine = p->engine == 2 && paired2 ? 2 + p->packed : p->engine;
+            chosen->pass2_threads = paired2 ? p->p2_ts : p->p2_threads;
             chosen->pass2_bulk_copy = p->tma ? 1 : 0;
             chosen->fused = p->fused ? 1 : 0;
             chosen->cells_per_launch = p->cell_batch;

@@ -213,14 +213,15 @@ def test_autotune_keeps_results(fs):
     p0.close()
     p = plan()
     t = p.autotune(64)
-    assert t["engine"] in (1, 2, 3, 4) and t["pass2_threads"] in (128, 256)
+    assert t["engine"] in (1, 2, 3, 4) and t["pass2_threads"] in (32, 128, 256)
     assert t["cells_per_launch"] >= 1 and t["ms_per_cell"] > 0
     assert p.candidates()[1] == 0                      # tuning searches are discarded
     p.search()
     c, _ = p.candidates()
     p.close()
-    default = t["engine"] == 3 and t["pass2_threads"] == 128 and t["pass2_bulk_copy"] == 1 and t["fused"] == 0
-    if default:                      # the default kernels: bit for bit
+    # the default kernels (the paired rows in one- or four-row CTAs compute the same): bit for bit
+    default = t["engine"] == 3 and t["pass2_threads"] in (32, 128) and t["pass2_bulk_copy"] == 1 and t["fused"] == 0
+    if default:
         assert np.array_equal(c, ref)
     else:
         keys = ("sky", "spin", "bin")
