@@ -359,7 +359,12 @@ void create_impl(Plan &p, const fstat_plan_desc *d) {
         p.w_stride = std::max<int64_t>(p.w_stride, (b.n + n1 - 1) / n1 * n1);
     }
     const int64_t nblk = (p.n_max + 255) / 256;
-    p.sky_batch = fp32 ? std::min<int64_t>(d->n_sky, 64) : 1;
+    // sky positions per batch: 64, or up to 256 when the spindowns are few, so that a
+    // batch holds the 4096 cells of a launch pair
+    p.sky_batch = fp32 ? std::min<int64_t>(d->n_sky, std::max<int64_t>(64, std::min<int64_t>(256, (4096 + d->n_spin - 1) / d->n_spin)))
+                       : 1;
+    if (fp32)
+        if (const char *v = getenv("FSTAT_SKY_BATCH")) p.sky_batch = std::max<int64_t>(1, std::min<int64_t>(d->n_sky, atoll(v)));
     const size_t w_elem = fp32 ? 16 : 32;
     for (int q = 0; q < 2; ++q) {
         p.wbuf[q] = dalloc<unsigned char>(p, (size_t)p.sky_batch * p.w_stride * w_elem, n_alloc);
