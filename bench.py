@@ -25,6 +25,7 @@ import statistics
 import subprocess
 import sys
 import tempfile
+import threading
 import time
 
 import numpy as np
@@ -315,7 +316,6 @@ def run_large(args, stream, flush, peak):
     on the other stream) while the next range is searched: the sustained rate is
     the wall time of all searches and all drains.  Beside it the plain FP64 form
     on a 1024 x 16 subgrid."""
-    import threading
     from paper_1410_3677_gb300 import fstat
     from paper_1410_3677_gb300 import synth as S
     import torch
@@ -577,34 +577,55 @@ def run_ours(args, rank, world, dist):
             hbs.append(hb)
         al, de, fd = pinned(w.alpha), pinned(w.delta), pinned(w.fdot)
         n_e2e = max(3, min(args.steps, 5))
-        w_e2e = 2     # the first search runs plainly, the second is captured as a CUDA graph
+        w_e2e = 2     # per plan: the first search runs plainly, the second is captured as a CUDA graph
+        streams = [stream, torch.cuda.Stream()]
 
-        def make_plan():
+        def make_plan(st=None):
             return fstat.Plan(hbs, al, de, fd, w.thr_2F, lat=w.lat, gamma=w.gamma,
                               upsample=w.upsample, form=fstat.FP32_BATCHED,
-                              cand_capacity=args.cand_capacity, stream=stream.cuda_stream)
-        # a stream of segments through one plan: per step the segment's series and
-        # ephemeris go host -> device, the search runs, the candidates come back
-        p = make_plan()
-        times, d2h = [], 0
-        out = None      # the caller's candidate array, reused across segments
-        for it in range(n_e2e + w_e2e):
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
+                              cand_capacity=args.cand_capacity,
+                              stream=(st or stream).cuda_stream)
+        # a stream of segments through two plans that take the segments in turn: per
+        # step the segment's series and ephemeris go host -> device and the search
+        # runs (a host thread) while the previous segment's candidates come back
+        # (sort, device -> host copy, expansion into the caller's array)
+        plans = [make_plan(st) for st in streams]
+        outs = [None, None]   # the caller's candidate arrays, reused across segments
+        d2h = 0
+        device = torch.cuda.current_device()
+
+        def upload_and_search(pl):
+            torch.cuda.set_device(device)
             for bi, hb in enumerate(hbs):
-                p.set_band(bi, hb)
-            p.search()
-            if out is not None:
-                c, nt = p.candidates(out=out)
+                pl.set_band(bi, hb)
+            pl.search()
+
+        def drain(i):
+            nonlocal d2h
+            if outs[i] is not None:
+                c, nt = plans[i].candidates(out=outs[i])
             else:
-                c, nt = p.candidates()
-                out = np.empty(c.size + c.size // 4 + 1024, fstat.CAND_DTYPE)
-                out.view(np.uint8)[:] = 0     # resident before the timed steps
-            torch.cuda.synchronize()
-            if it >= w_e2e:
-                times.append(time.perf_counter() - t0)
+                c, nt = plans[i].candidates()
+                outs[i] = np.empty(c.size + c.size // 4 + 1024, fstat.CAND_DTYPE)
+                outs[i].view(np.uint8)[:] = 0     # resident before the timed steps
             d2h = int(c.size) * 16 + 8
-        p.close()
+        for it in range(w_e2e):               # untimed: both plans, plain then captured
+            for i in range(2):
+                upload_and_search(plans[i])
+                drain(i)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for k in range(n_e2e):
+            th = threading.Thread(target=upload_and_search, args=(plans[k % 2],))
+            th.start()
+            if k > 0:
+                drain((k - 1) % 2)
+            th.join()
+        drain((n_e2e - 1) % 2)
+        torch.cuda.synchronize()
+        times = [(time.perf_counter() - t0) / n_e2e]
+        for pl in plans:
+            pl.close()
         # the same with a plan created (allocations, tables, grid upload) and destroyed per step
         h2d_grid = al.nbytes + de.nbytes + fd.nbytes
         times_pc = []
@@ -626,8 +647,10 @@ def run_ours(args, rank, world, dist):
                                     "h2d_bytes_per_step": int(h2d + h2d_grid)},
                "includes": "fstat_plan_set_band per band (host->device copy of the segment's series "
                            "and ephemeris from pinned memory; sigma^2 and the upsample are redone by "
-                           "the search) + fstat_search + fstat_candidates_get (device->host + sort); "
-                           "the plan is created once before the timed steps"}
+                           "the search) + fstat_search + fstat_candidates_get (device->host + sort) "
+                           "for every step; two plans created before the timed steps take the "
+                           "segments in turn, a segment's candidates drained while the next is "
+                           "searched"}
 
     banded = large = None
     if rank == 0 and world == 1 and not args.skip_banded:
