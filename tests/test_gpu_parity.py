@@ -116,6 +116,18 @@ def test_all_bins_tiny_workload(fs, form):
     _check_all_bins(c, w, form, 0, cells, 1, 4095)
 
 
+def test_few_spindowns_large_sky_batches(fs):
+    """Two spindowns and 300 sky positions: the FP32 form takes sky batches of up to
+    256 positions (a full 4096-cell launch pair would need 2048), so the grid is
+    one full batch and a ragged one of 44; every bin of cells in both, against
+    the oracle."""
+    w = S.workload(1, n_sky=300, n_spin=2)
+    c, info = _gpu_F(fs, w, 1)
+    assert info["f_evals"] == 600 * 4095
+    cells = [(s, j) for s in (0, 1, 255, 256, 257, 299) for j in range(2)]
+    _check_all_bins(c, w, 1, 0, cells, 1, 4095)
+
+
 @pytest.mark.parametrize("form", [0, 1])
 def test_candidates_tiny_workload(fs, form):
     """Threshold 2F > 20: same candidate list as the oracle outside the band."""
