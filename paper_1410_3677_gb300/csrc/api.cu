@@ -497,9 +497,10 @@ void free_all(Plan &p) {
     p.stream = nullptr;
     p.own_stream = false;
     if (p.h_rec) cudaFreeHost(p.h_rec);
-    if (p.h_tmp) cudaFreeHost(p.h_tmp);
-    p.h_rec = p.h_tmp = nullptr;
+    p.h_rec = nullptr;
     p.h_rec_cap = 0;
+    p.h_tmp.clear();
+    p.h_tmp.shrink_to_fit();
     if (p.cand_tmp) cudaFree(p.cand_tmp);
     if (p.sort_hist) cudaFree(p.sort_hist);
     p.cand_tmp = nullptr;
@@ -999,22 +1000,22 @@ fstat_status fstat_candidates_get(fstat_plan *p, fstat_candidate *buf, int64_t c
         const int64_t kept = std::min<int64_t>(p->last_total, p->cand_capacity);
         if (kept > p->h_rec_cap) {   // pinned staging, reused: no page faults, full-rate copies
             if (p->h_rec) cudaFreeHost(p->h_rec);
-            if (p->h_tmp) cudaFreeHost(p->h_tmp);
-            p->h_rec = p->h_tmp = nullptr;
+            p->h_rec = nullptr;
             p->h_rec_cap = 0;
             const int64_t want = std::max<int64_t>(kept, kept + kept / 4);
-            if (cudaHostAlloc((void **)&p->h_rec, want * sizeof(CandRecord), cudaHostAllocDefault) != cudaSuccess ||
-                cudaHostAlloc((void **)&p->h_tmp, want * sizeof(CandRecord), cudaHostAllocDefault) != cudaSuccess) {
+            if (cudaHostAlloc((void **)&p->h_rec, want * sizeof(CandRecord), cudaHostAllocDefault) != cudaSuccess) {
                 cudaGetLastError();
-                if (p->h_rec) cudaFreeHost(p->h_rec);
-                p->h_rec = p->h_tmp = nullptr;
+                p->h_rec = nullptr;
                 throw std::bad_alloc();
             }
             p->h_rec_cap = want;
         }
-        CandRecord *rec = p->h_rec, *tmp = p->h_tmp;
+        CandRecord *rec = p->h_rec;
         // many records: sorted on the device once per search, then read back in order
         const bool dev_sort = kept >= kDeviceSortMin && kept < (int64_t(1) << 32) - kTileSlack;
+        // a few records: sorted on the host, with a pageable work array (no pinning)
+        if (!dev_sort && (int64_t)p->h_tmp.size() < kept) p->h_tmp.resize((size_t)kept);
+        CandRecord *tmp = p->h_tmp.data();
         if (dev_sort && !p->cand_sorted) {
             if (kept > p->sort_cap) {
                 if (p->cand_tmp) cudaFree(p->cand_tmp);

@@ -158,7 +158,8 @@ struct Plan {
     int64_t cand_capacity = 0;
     // pinned host staging of the candidate records (read back and sorted there),
     // grown on demand and reused by later calls
-    CandRecord *h_rec = nullptr, *h_tmp = nullptr;
+    CandRecord *h_rec = nullptr;           // pinned staging of the read-back
+    std::vector<CandRecord> h_tmp;         // work array of the host sort (few records)
     int64_t h_rec_cap = 0;
     // device sort of the records before the read-back: the other ping-pong buffer,
     // the digit counts, the cell range of the records and the sorted buffer (null
