@@ -406,6 +406,7 @@ void create_impl(Plan &p, const fstat_plan_desc *d) {
         if (const char *v = getenv("FSTAT_PF_DIST")) p.pf_dist = std::max(0, atoi(v));
         if (const char *v = getenv("FSTAT_PF_DIST_PAIRED")) p.pf_dist_pk = std::max(0, atoi(v));
         if (const char *v = getenv("FSTAT_SHARE_CHIRP")) p.share_chirp = atoi(v) != 0;
+        if (const char *v = getenv("FSTAT_P2_ROWS")) p.p2_rows = atoi(v) != 0;
         if (const char *v = getenv("FSTAT_P2_TS")) {
             const int ts = atoi(v);
             p.p2_ts = ts == 64 || ts == 128 ? ts : 32;

@@ -141,6 +141,7 @@ struct Plan {
     int64_t pf_dist_pk = 0;        // the same for the paired pass 2 (measured best off)
     bool share_chirp = true;       // pass 1: spindown phase shared by the lanes of a column
     int p2_ts = 32;                // paired pass 2: CTA size (32, 64 or 128: one warp per row)
+    bool p2_rows = true;           // 256-point rows (2^16, 2^17): two rows per warp, packed
     bool tma = true;               // two-stage pass 2: rows staged by bulk copies
     int p2_threads = 128;          // two-stage pass 2 with bulk copies: CTA size 256 or 128
 

@@ -1,6 +1,6 @@
 // The FP32 search passes in packed arithmetic (packed.cuh) for passes of length
 // 512: both passes at N_fft = 2^18 (N1 = N2 = 512, the two-sidereal-day
-// segments), the rows (pass 2) at 2^19.  Same four-step split, scratch layout, tiles and
+// segments), the rows (pass 2) at 2^19; and the 256-point rows of 2^16 and 2^17.  Same four-step split, scratch layout, tiles and
 // launch shapes as the second engine's passes (passes2.cuh); what changes is how
 // a thread's 32 elements are transformed:
 //
@@ -323,6 +323,147 @@ k_pass2p(ScratchLoadTMA<Cfg2<LOGN, 2, TS>> ld, SearchEpi2<Cfg2<LOGN, 2, TS>, LOW
     for (int r = 1; r < 16; ++r) Q[r] = pk::cmul(Q[r], tw1(tws, r, j));
     pk::dft16<16, LOWER>(Q);
     epilogue<C, LOWER>(ep, t, j, l2, Q);
+}
+
+// --------------------------------------------------------------------- pass 2, 256-point rows
+// The rows of N_fft = 2^16 and 2^17 (N1 = 256 = 16 x 16) with two adjacent rows
+// per warp and CTA, the rows packed in pairs: every operation is the same for
+// rows l2 and l2 + 1 except the four-step twiddle, which comes as a pair.
+// Lane 2j + t (t the transform) takes the elements k1 = j + 16 m of both rows;
+// stage 0 is a packed 16-point DFT over m (after the twiddle W_N^{l2 k1}),
+// stage 1 for job q the twiddle W_256^{j q} and a packed 16-point DFT over j,
+// giving l1 = q + 16 p.  The exchange lies over the warp's staged 8 KiB.
+template <class C, bool LOWER>
+__device__ __forceinline__ void epilogue_rows(const SearchEpi2<C, LOWER> &ep, int t, int q, int l2, const PC *Y) {
+    constexpr int NP = LOWER ? 8 : 16;   // outputs p used
+    constexpr int H = NP / 2;
+    const int lane = (int)threadIdx.x & 31;
+    const bool full = ep.nab != 0.f;
+    float2 Fv[H];   // (row l2, row l2 + 1)
+#pragma unroll
+    for (int u = 0; u < H; ++u) {
+        const PC lo = Y[u], hi = Y[u + H];
+        if (full) {
+            const PC send = t == 0 ? hi : lo, mine = t == 0 ? lo : hi;
+            PC oth;
+            oth.re.x = __shfl_xor_sync(0xffffffffu, send.re.x, 1);
+            oth.re.y = __shfl_xor_sync(0xffffffffu, send.re.y, 1);
+            oth.im.x = __shfl_xor_sync(0xffffffffu, send.im.x, 1);
+            oth.im.y = __shfl_xor_sync(0xffffffffu, send.im.y, 1);
+            const PC a = t == 0 ? mine : oth, b = t == 0 ? oth : mine;
+            const float2 pa = pk::pfma(a.re, a.re, pk::pmul(a.im, a.im));
+            const float2 pb = pk::pfma(b.re, b.re, pk::pmul(b.im, b.im));
+            const float2 cr = pk::pfma(a.re, b.re, pk::pmul(a.im, b.im));
+            Fv[u] = pk::pfma(pa, pk::bc(ep.na), pk::pfma(pb, pk::bc(ep.nb), pk::pmul(cr, pk::bc(ep.nab))));
+        } else {
+            const float2 plo = pk::pfma(lo.re, lo.re, pk::pmul(lo.im, lo.im));
+            const float2 phi = pk::pfma(hi.re, hi.re, pk::pmul(hi.im, hi.im));
+            const float2 ps = t == 0 ? phi : plo, pm = t == 0 ? plo : phi;
+            float2 po;
+            po.x = __shfl_xor_sync(0xffffffffu, ps.x, 1);
+            po.y = __shfl_xor_sync(0xffffffffu, ps.y, 1);
+            const float2 pa = t == 0 ? pm : po, pb = t == 0 ? po : pm;
+            Fv[u] = pk::pfma(pa, pk::bc(ep.na), pk::pmul(pb, pk::bc(ep.nb)));
+        }
+    }
+    // bins: output p = u + t H of job q: l1 = q + 16 p, bin = N2 l1 + l2 + e
+    const int lo = (int)ep.bin_lo;
+    const unsigned span = (unsigned)(ep.bin_hi - ep.bin_lo);
+    const int bin0 = C::N2 * (q + 16 * t * H) + l2;
+    bool pr[2 * H];
+    bool any = false;
+#pragma unroll
+    for (int u = 0; u < H; ++u)
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+            const int bin = bin0 + C::N2 * 16 * u + e;
+            const float f = e ? Fv[u].y : Fv[u].x;
+            pr[2 * u + e] = ((unsigned)(bin - lo) <= span) && (f > ep.thr_half);
+            any |= pr[2 * u + e];
+        }
+    if (!__any_sync(0xffffffffu, any)) return;
+#pragma unroll
+    for (int u = 0; u < H; ++u)
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+            const bool hit = pr[2 * u + e];
+            const unsigned m = __ballot_sync(0xffffffffu, hit);
+            if (m) {
+                const int leader = __ffs(m) - 1;
+                unsigned long long b0 = 0;
+                if (lane == leader) b0 = atomicAdd(ep.count, (unsigned long long)__popc(m));
+                b0 = __shfl_sync(0xffffffffu, b0, leader);
+                if (hit) {
+                    const unsigned long long idx = b0 + __popc(m & ((1u << lane) - 1u));
+                    const float f = e ? Fv[u].y : Fv[u].x;
+                    if (idx < ep.cap)
+                        ep.out[idx] = CandRecord{ep.cell, (uint32_t)(bin0 + C::N2 * 16 * u + e), (double)f};
+                }
+            }
+        }
+}
+
+template <int LOGN, bool LOWER>
+__global__ void __launch_bounds__(32, 24)
+k_pass2r(ScratchLoadTMA<Cfg2<LOGN, 2, 32>> ld, SearchEpi2<Cfg2<LOGN, 2, 32>, LOWER> ep,
+         const float2 *__restrict__ w256) {
+    using C = Cfg2<LOGN, 2, 32>;
+    static_assert(C::M == 256 && C::F == 2 && C::THREADS == 32, "256-point rows, two per warp");
+    ld.prefetch_ahead();
+    ld.init(blockIdx.x, blockIdx.y, blockIdx.y);
+    ld.bar = reinterpret_cast<uint64_t *>(eng2::dyn_smem() + 2 * C::F * C::N1 * sizeof(float2));
+    const int lane = (int)threadIdx.x & 31;
+    ep.init(blockIdx.x, blockIdx.y, blockIdx.y);
+    ld.stage();
+    const int t = lane & 1, j = lane >> 1;
+    const int l2 = ld.l2_0;   // rows l2 and l2 + 1
+    // four-step factors of the two rows: T_0 = W^{l2 j}, step W^{16 l2}
+    const float2 wa = ld.tw.wn(l2 * j), wb = ld.tw.wn((l2 + 1) * j);
+    const float2 sa = ld.tw.wn(16 * l2), sb = ld.tw.wn(16 * (l2 + 1));
+    PC T = {make_float2(wa.x, wb.x), make_float2(wa.y, wb.y)};
+    const PC S = {make_float2(sa.x, sb.x), make_float2(sa.y, sb.y)};
+    if (!ptx::mbar_try_wait(ld.bar, 0)) {   // bounded wait, as ScratchLoadTMA::load
+        const uint64_t t0 = ptx::globaltimer_ns();
+        bool late = false;
+        while (!ptx::mbar_try_wait(ld.bar, 0)) {
+            const uint64_t dt = ptx::globaltimer_ns() - t0;
+            if (!late && dt > 1000000000ull) { atomicExch(ld.err, 1u); late = true; }
+            if (dt > 2000000000ull) break;   // reported above; results are discarded
+        }
+    }
+    PC P[16];
+    {
+        const float2 *ra = ld.rows + 2 * j + t, *rb = ra + 2 * C::N1;   // element k1 at r[2 k1]
+#pragma unroll
+        for (int m = 0; m < 16; ++m) {
+            const float2 a = ra[2 * 16 * m], b = rb[2 * 16 * m];
+            P[m] = pk::cmul({make_float2(a.x, b.x), make_float2(a.y, b.y)}, T);
+            if (m + 1 < 16) T = pk::cmul(T, S);
+        }
+    }
+    pk::dft16<16>(P);   // P[k] = Z_j[k] of both rows
+    __syncwarp();       // the staged rows have been read: the exchange may overwrite them
+    float4 *ex = reinterpret_cast<float4 *>(eng2::dyn_smem()) + t * 256;
+    const int jx = j ^ (4 * t);
+#pragma unroll
+    for (int k = 0; k < 16; ++k) ex[k * 16 + (jx ^ k)] = make_float4(P[k].re.x, P[k].re.y, P[k].im.x, P[k].im.y);
+    __syncwarp();
+    // stage 1, job q = j: the butterflies r of output q, twiddled by W_256^{r q}
+    const int q = j;
+    PC Q[16];
+#pragma unroll
+    for (int r = 0; r < 16; ++r) {
+        const float4 v = ex[q * 16 + (r ^ jx)];
+        Q[r] = {make_float2(v.x, v.y), make_float2(v.z, v.w)};
+    }
+#pragma unroll
+    for (int r = 1; r < 16; ++r) {
+        const float2 w = __ldg(w256 + ((r * q) & 255));
+        Q[r] = {pk::pfma(Q[r].re, pk::bc(w.x), pk::pmul(Q[r].im, pk::bc(-w.y))),
+                pk::pfma(Q[r].re, pk::bc(w.y), pk::pmul(Q[r].im, pk::bc(w.x)))};
+    }
+    pk::dft16<16, LOWER>(Q);   // Y[q + 16 p], p < 8 (LOWER) or 16
+    epilogue_rows<C, LOWER>(ep, t, q, l2, Q);
 }
 
 }  // namespace p3

@@ -118,6 +118,24 @@ int launch_two(const Plan &p, int band_idx, const BandDev &b, int64_t s0, int64_
         k1<<<dim3(C1::TILES, (unsigned)nc), C1::THREADS, C1::SMEM, s>>>(ld1, st1, tw->s2_f);
     }
     if (mid) record_timing_event(mid, s);
+    if constexpr (LOGN == 16 || LOGN == 17) {   // 256-point rows: two per warp, packed
+        if (p.packed >= 1 && p.tma && p.p2_threads != 256 && p.p2_rows) {
+            using D2 = Cfg2<LOGN, 2, 32>;
+            ScratchLoadTMA<D2> lt{};
+            lt.scratch = ld2.scratch;
+            lt.tw = ld2.tw;
+            lt.pf_dist = 0;
+            lt.err = p.qerr;
+            const auto ep = make_epi<LOGN, LOWER, 32>(p, band_idx, b, c0, s0, cb);
+            auto k2 = p3::k_pass2r<LOGN, LOWER>;
+            constexpr size_t smem2 = (size_t)2 * D2::F * D2::N1 * sizeof(float2) + 16;   // staged rows + mbarrier
+            static bool attr2r = false;
+            if (!attr2r) { set_smem(k2, smem2); attr2r = true; }
+            k2<<<dim3(D2::TILES, (unsigned)nc), D2::THREADS, smem2, s>>>(
+                lt, ep, reinterpret_cast<const float2 *>(tw->in1_f));
+            return 2;
+        }
+    }
     if constexpr (LOGN == 18 || LOGN == 19) {
         if (pk2) {
             if (p.p2_ts == 32) launch_pass2p<LOGN, LOWER, 32>(p, band_idx, b, s0, c0, nc, s, cb, ld2, tw);

@@ -113,6 +113,34 @@ def test_engines_agree_on_every_bin(fs, n, n_fft):
     assert np.all(np.abs(a["F"] - b["F"]) <= 2e-4 * np.maximum(np.maximum(a["F"], b["F"]), 2.0))
 
 
+@pytest.mark.parametrize("n,n_fft,full,rows", [(30000, 1 << 16, False, "1"), (60000, 1 << 17, False, "1"),
+                                               (43082, 1 << 17, True, "1"), (60000, 1 << 17, False, "0")])
+def test_row_pairs_against_oracle_every_bin(fs, n, n_fft, full, rows):
+    """The 256-point rows (N_fft = 2^16, 2^17) two per warp in packed arithmetic (the
+    default) and in the scalar two-stage pass: every bin of every cell against the
+    FP64 oracle at the FP32 tolerance, with the simple and the full (cross-term)
+    statistic."""
+    import oracle as O
+    w0 = S.workload(1, n_sky=3, n_spin=2)
+    b = S.make_band(n, 2.0, 77 + n, 1.0, w0.alpha, w0.delta, w0.fdot, [], n_fft=n_fft,
+                    f_off=100 + (1 - 2 ** -5) * 3)
+    w = S.Workload("row-pairs", [b], w0.alpha, w0.delta, w0.fdot, 10.0, upsample=2)
+    env = {"FSTAT_PERSISTENT": "0", "FSTAT_P2_ROWS": rows}
+    p, rc, c, total = _run(fs, w, -1.0, env, full=full)
+    p.close()
+    nb = n_fft // 2 - 1
+    assert rc == fs.FSTAT_OK and total == 6 * nb
+    prm = O.params(w.lat, w.gamma, w.upsample, 0.0, full, 0)
+    cells = [(s, j) for s in range(3) for j in range(2)]
+    ref = O.cells_F(b, prm, w.alpha, w.delta, w.fdot, np.array([x[0] for x in cells]),
+                    np.array([x[1] for x in cells]), 0, 0, os.cpu_count() or 4)
+    for i, (sk, sp) in enumerate(cells):
+        sel = c[(c["sky"] == sk) & (c["spin"] == sp)]
+        assert np.array_equal(sel["bin"], np.arange(1, nb + 1))
+        err = np.abs(sel["F"] - ref[i]) / np.maximum(ref[i], 2.0)
+        assert err.max() <= 1e-4, (n_fft, full, sk, sp, err.max())
+
+
 def test_queue_cell_ranges(fs):
     """Ranges that start and end inside a sky position and a batch."""
     w = S.workload(1, n_sky=7, n_spin=5)
