@@ -141,6 +141,48 @@ def test_row_pairs_against_oracle_every_bin(fs, n, n_fft, full, rows):
         assert err.max() <= 1e-4, (n_fft, full, sk, sp, err.max())
 
 
+def test_two_plans_in_two_threads(fs):
+    """Two plans on two streams searched from two host threads at once (the way the
+    benchmark overlaps one range's candidate drain with the next range's search):
+    each returns bit for bit what one plan returns for its cell range."""
+    import threading
+    import torch
+    w = S.workload(3, n_sky=12, n_spin=8)
+    cells = w.n_sky * w.n_spin
+    half = cells // 2
+    p0, rc0, _, _ = _run(fs, w, w.thr_2F, DEFAULT)
+    ref = []
+    for lo, hi in ((0, half), (half, cells)):
+        p0.search(lo, hi)
+        ref.append(p0.candidates()[0])
+    p0.close()
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    plans = [fs.Plan(w.bands, w.alpha, w.delta, w.fdot, w.thr_2F, lat=w.lat, gamma=w.gamma,
+                     upsample=w.upsample, form=fs.FP32_BATCHED, cand_capacity=1 << 22,
+                     stream=st.cuda_stream) for st in streams]
+    device = torch.cuda.current_device()
+    errors = []
+
+    def run(i, lo, hi):
+        try:
+            torch.cuda.set_device(device)
+            for _ in range(3):               # plain, captured, replayed
+                plans[i].search(lo, hi)
+        except Exception as e:               # reported to the main thread
+            errors.append(e)
+    th = [threading.Thread(target=run, args=(0, 0, half)), threading.Thread(target=run, args=(1, half, cells))]
+    for t in th:
+        t.start()
+    for t in th:
+        t.join()
+    assert not errors
+    got = [pl.candidates()[0] for pl in plans]
+    for pl in plans:
+        pl.close()
+    for a, b in zip(ref, got):
+        assert np.array_equal(a, b)
+
+
 def test_queue_cell_ranges(fs):
     """Ranges that start and end inside a sky position and a batch."""
     w = S.workload(1, n_sky=7, n_spin=5)
