@@ -31,7 +31,9 @@
  * Conventions for every entry point:
  *   - returns an fstat_status; nothing throws across the ABI;
  *   - calls are synchronous with respect to the host (they return after the GPU
- *     work they queue has finished); a plan is not thread-safe;
+ *     work they queue has finished); a plan is not thread-safe, but different
+ *     plans (each on its own stream) may be used from different host threads at
+ *     the same time (their graph captures are thread-local);
  *   - the caller owns every array it passes and may free it after the call that
  *     received it returns; the plan owns all device memory it allocates;
  *   - after FSTAT_ERR_CUDA or FSTAT_ERR_TIMEOUT a plan is poisoned: later calls
