@@ -49,23 +49,32 @@ __device__ double block_sum256(double v, double *sh) {
     return r;
 }
 
-// The same for FP32 terms: each warp adds its 32 terms in FP32 (relative error
-// ~1e-7), the block adds the warp sums in FP64; the blocks' partials are then
-// added with compensation.  The FP32 form's S sums thus keep FP64 accumulation
-// where the term count is large, and spend no FP64 instructions per sample.
-__device__ double block_sum256_f(float v, double *sh) {
+// The FP32 form's three S terms at once: each warp adds its 32 terms of each in
+// FP32 (relative error ~1e-7), one barrier, then three threads add the block's
+// warp sums in FP64 and write the block's partials (blockDim.x = 256); the
+// blocks' partials are then added with compensation.  The S sums thus keep FP64
+// accumulation where the term count is large, and spend no FP64 instructions per
+// sample.
+__device__ void block_sum3_f(float a, float b, float c, double *sh, double *out) {
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_down_sync(0xffffffffu, a, o);
+        b += __shfl_down_sync(0xffffffffu, b, o);
+        c += __shfl_down_sync(0xffffffffu, c, o);
+    }
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-    if (l == 0) sh[w] = (double)v;
-    __syncthreads();
-    double r = 0.0;
-    if (w == 0) {
-        r = (l < (int)(blockDim.x >> 5)) ? sh[l] : 0.0;
-        r = warp_sum(r);
+    if (l == 0) {
+        sh[w] = (double)a;
+        sh[8 + w] = (double)b;
+        sh[16 + w] = (double)c;
     }
     __syncthreads();
-    return r;
+    if (threadIdx.x < 3) {
+        double t = 0.0;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) t += sh[8 * threadIdx.x + i];
+        out[threadIdx.x] = t;
+    }
 }
 
 // ------------------------------------------------------------------ sigma^2
@@ -202,7 +211,7 @@ __global__ void __launch_bounds__(256) k_delays_split(const DF *__restrict__ r2,
 
 template <bool FP32>
 __global__ void __launch_bounds__(256) k_geometry(GeoArgs g) {
-    __shared__ double sh[8];
+    __shared__ double sh[24];
     const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const int sl = blockIdx.y;
     double saa = 0.0, sbb = 0.0, sab = 0.0;    // FP64 form
@@ -346,19 +355,16 @@ __global__ void __launch_bounds__(256) k_geometry(GeoArgs g) {
             }
         }
     }
-    double ta, tb, tab;
+    double *o = g.partials + ((int64_t)sl * g.nblk + blockIdx.x) * 3;
     if constexpr (FP32) {
-        ta = block_sum256_f(saa_f, sh);
-        tb = block_sum256_f(sbb_f, sh);
-        tab = block_sum256_f(sab_f, sh);
+        block_sum3_f(saa_f, sbb_f, sab_f, sh, o);
     } else {
-        ta = block_sum256(saa, sh);
-        tb = block_sum256(sbb, sh);
-        tab = block_sum256(sab, sh);
-    }
-    if (threadIdx.x == 0) {
-        double *o = g.partials + ((int64_t)sl * g.nblk + blockIdx.x) * 3;
-        o[0] = ta; o[1] = tb; o[2] = tab;
+        const double ta = block_sum256(saa, sh);
+        const double tb = block_sum256(sbb, sh);
+        const double tab = block_sum256(sab, sh);
+        if (threadIdx.x == 0) {
+            o[0] = ta; o[1] = tb; o[2] = tab;
+        }
     }
 }
 
