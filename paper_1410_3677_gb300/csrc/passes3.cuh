@@ -171,14 +171,20 @@ __host__ __device__ constexpr size_t pass2p_smem() {
     return (size_t)2 * C::F * C::N1 * sizeof(float2);
 }
 
-// F per bin of the packed outputs (the epilogue of SearchEpi2 on pairs of jobs).
+// Outputs p of a packed 16-point DFT that the F epilogue uses, halved: the bin
+// range below N/2 (LOWER) needs p < 8 only.
+template <bool LOWER>
+__host__ __device__ constexpr int epi_half() { return (LOWER ? 8 : 16) / 2; }
+
+// F per bin of the packed outputs (the epilogue of SearchEpi2 on pairs of values).
 // Lanes 2j (F_a) and 2j + 1 (F_b) hold the same bins; the a lane evaluates F on
 // the outputs p < H, the b lane on p >= H, each taking the partner's values for
-// its half with one shuffle per value.
+// its half with one shuffle per value.  Output u of this lane's half, pair member
+// e, is bin bin0 + u step_u + e step_e.
 template <class C, bool LOWER>
-__device__ __forceinline__ void epilogue(const SearchEpi2<C, LOWER> &ep, int t, int jp, int l2, const PC *Y) {
-    constexpr int NP = LOWER ? 8 : 16;   // outputs p of each job used
-    constexpr int H = NP / 2;
+__device__ __forceinline__ void epilogue(const SearchEpi2<C, LOWER> &ep, int t, int bin0, int step_u, int step_e,
+                                         const PC *Y) {
+    constexpr int H = epi_half<LOWER>();
     const int lane = (int)threadIdx.x & 31;
     const bool full = ep.nab != 0.f;
     float2 Fv[H];
@@ -210,17 +216,15 @@ __device__ __forceinline__ void epilogue(const SearchEpi2<C, LOWER> &ep, int t, 
             Fv[u] = pk::pfma(pa, pk::bc(ep.na), pk::pmul(pb, pk::bc(ep.nb)));
         }
     }
-    // bins: job jj = 2 jp + e, output p = u + t H: l1 = jj + 32 p, bin = N2 l1 + l2 (< 2^19)
-    const int lo = (int)ep.bin_lo;
+    const int lo = (int)ep.bin_lo;   // bins < 2^19
     const unsigned span = (unsigned)(ep.bin_hi - ep.bin_lo);
-    const int bin0 = C::N2 * (2 * jp + kR0 * t * H) + l2;
     bool pr[2 * H];
     bool any = false;
 #pragma unroll
     for (int u = 0; u < H; ++u)
 #pragma unroll
         for (int e = 0; e < 2; ++e) {
-            const int bin = bin0 + C::N2 * (e + kR0 * u);
+            const int bin = bin0 + step_u * u + step_e * e;
             const float f = e ? Fv[u].y : Fv[u].x;
             pr[2 * u + e] = ((unsigned)(bin - lo) <= span) && (f > ep.thr_half);
             any |= pr[2 * u + e];
@@ -241,7 +245,7 @@ __device__ __forceinline__ void epilogue(const SearchEpi2<C, LOWER> &ep, int t, 
                     const unsigned long long idx = b0 + __popc(m & ((1u << lane) - 1u));
                     const float f = e ? Fv[u].y : Fv[u].x;
                     if (idx < ep.cap)
-                        ep.out[idx] = CandRecord{ep.cell, (uint32_t)(bin0 + C::N2 * (e + kR0 * u)), (double)f};
+                        ep.out[idx] = CandRecord{ep.cell, (uint32_t)(bin0 + step_u * u + step_e * e), (double)f};
                 }
             }
         }
@@ -322,7 +326,9 @@ k_pass2p(ScratchLoadTMA<Cfg2<LOGN, 2, TS>> ld, SearchEpi2<Cfg2<LOGN, 2, TS>, LOW
 #pragma unroll
     for (int r = 1; r < 16; ++r) Q[r] = pk::cmul(Q[r], tw1(tws, r, j));
     pk::dft16<16, LOWER>(Q);
-    epilogue<C, LOWER>(ep, t, j, l2, Q);
+    // bins: job 2j + e, output p = u + t H: l1 = 2j + e + 32 p, bin = N2 l1 + l2
+    constexpr int H = epi_half<LOWER>();
+    epilogue<C, LOWER>(ep, t, C::N2 * (2 * j + kR0 * t * H) + l2, C::N2 * kR0, C::N2, Q);
 }
 
 // --------------------------------------------------------------------- pass 2, 256-point rows
@@ -333,76 +339,6 @@ k_pass2p(ScratchLoadTMA<Cfg2<LOGN, 2, TS>> ld, SearchEpi2<Cfg2<LOGN, 2, TS>, LOW
 // stage 0 is a packed 16-point DFT over m (after the twiddle W_N^{l2 k1}),
 // stage 1 for job q the twiddle W_256^{j q} and a packed 16-point DFT over j,
 // giving l1 = q + 16 p.  The exchange lies over the warp's staged 8 KiB.
-template <class C, bool LOWER>
-__device__ __forceinline__ void epilogue_rows(const SearchEpi2<C, LOWER> &ep, int t, int q, int l2, const PC *Y) {
-    constexpr int NP = LOWER ? 8 : 16;   // outputs p used
-    constexpr int H = NP / 2;
-    const int lane = (int)threadIdx.x & 31;
-    const bool full = ep.nab != 0.f;
-    float2 Fv[H];   // (row l2, row l2 + 1)
-#pragma unroll
-    for (int u = 0; u < H; ++u) {
-        const PC lo = Y[u], hi = Y[u + H];
-        if (full) {
-            const PC send = t == 0 ? hi : lo, mine = t == 0 ? lo : hi;
-            PC oth;
-            oth.re.x = __shfl_xor_sync(0xffffffffu, send.re.x, 1);
-            oth.re.y = __shfl_xor_sync(0xffffffffu, send.re.y, 1);
-            oth.im.x = __shfl_xor_sync(0xffffffffu, send.im.x, 1);
-            oth.im.y = __shfl_xor_sync(0xffffffffu, send.im.y, 1);
-            const PC a = t == 0 ? mine : oth, b = t == 0 ? oth : mine;
-            const float2 pa = pk::pfma(a.re, a.re, pk::pmul(a.im, a.im));
-            const float2 pb = pk::pfma(b.re, b.re, pk::pmul(b.im, b.im));
-            const float2 cr = pk::pfma(a.re, b.re, pk::pmul(a.im, b.im));
-            Fv[u] = pk::pfma(pa, pk::bc(ep.na), pk::pfma(pb, pk::bc(ep.nb), pk::pmul(cr, pk::bc(ep.nab))));
-        } else {
-            const float2 plo = pk::pfma(lo.re, lo.re, pk::pmul(lo.im, lo.im));
-            const float2 phi = pk::pfma(hi.re, hi.re, pk::pmul(hi.im, hi.im));
-            const float2 ps = t == 0 ? phi : plo, pm = t == 0 ? plo : phi;
-            float2 po;
-            po.x = __shfl_xor_sync(0xffffffffu, ps.x, 1);
-            po.y = __shfl_xor_sync(0xffffffffu, ps.y, 1);
-            const float2 pa = t == 0 ? pm : po, pb = t == 0 ? po : pm;
-            Fv[u] = pk::pfma(pa, pk::bc(ep.na), pk::pmul(pb, pk::bc(ep.nb)));
-        }
-    }
-    // bins: output p = u + t H of job q: l1 = q + 16 p, bin = N2 l1 + l2 + e
-    const int lo = (int)ep.bin_lo;
-    const unsigned span = (unsigned)(ep.bin_hi - ep.bin_lo);
-    const int bin0 = C::N2 * (q + 16 * t * H) + l2;
-    bool pr[2 * H];
-    bool any = false;
-#pragma unroll
-    for (int u = 0; u < H; ++u)
-#pragma unroll
-        for (int e = 0; e < 2; ++e) {
-            const int bin = bin0 + C::N2 * 16 * u + e;
-            const float f = e ? Fv[u].y : Fv[u].x;
-            pr[2 * u + e] = ((unsigned)(bin - lo) <= span) && (f > ep.thr_half);
-            any |= pr[2 * u + e];
-        }
-    if (!__any_sync(0xffffffffu, any)) return;
-#pragma unroll
-    for (int u = 0; u < H; ++u)
-#pragma unroll
-        for (int e = 0; e < 2; ++e) {
-            const bool hit = pr[2 * u + e];
-            const unsigned m = __ballot_sync(0xffffffffu, hit);
-            if (m) {
-                const int leader = __ffs(m) - 1;
-                unsigned long long b0 = 0;
-                if (lane == leader) b0 = atomicAdd(ep.count, (unsigned long long)__popc(m));
-                b0 = __shfl_sync(0xffffffffu, b0, leader);
-                if (hit) {
-                    const unsigned long long idx = b0 + __popc(m & ((1u << lane) - 1u));
-                    const float f = e ? Fv[u].y : Fv[u].x;
-                    if (idx < ep.cap)
-                        ep.out[idx] = CandRecord{ep.cell, (uint32_t)(bin0 + C::N2 * 16 * u + e), (double)f};
-                }
-            }
-        }
-}
-
 template <int LOGN, bool LOWER>
 __global__ void __launch_bounds__(32, 24)
 k_pass2r(ScratchLoadTMA<Cfg2<LOGN, 2, 32>> ld, SearchEpi2<Cfg2<LOGN, 2, 32>, LOWER> ep,
@@ -463,7 +399,9 @@ k_pass2r(ScratchLoadTMA<Cfg2<LOGN, 2, 32>> ld, SearchEpi2<Cfg2<LOGN, 2, 32>, LOW
                 pk::pfma(Q[r].re, pk::bc(w.y), pk::pmul(Q[r].im, pk::bc(w.x)))};
     }
     pk::dft16<16, LOWER>(Q);   // Y[q + 16 p], p < 8 (LOWER) or 16
-    epilogue_rows<C, LOWER>(ep, t, q, l2, Q);
+    // bins: output p = u + t H of job q for row l2 + e: l1 = q + 16 p, bin = N2 l1 + l2 + e
+    constexpr int H = epi_half<LOWER>();
+    epilogue<C, LOWER>(ep, t, C::N2 * (q + 16 * t * H) + l2, C::N2 * 16, 1, Q);
 }
 
 }  // namespace p3
